@@ -1,0 +1,147 @@
+"""Seeded synthetic workloads: problem statements and initial fields.
+
+This module only *describes* inputs.  It holds none of the method's arithmetic
+(no lattice constants, no equilibria, no parameter derivation): a problem is a
+plain dict of the paper's dimensionless groups and boundary conditions, and the
+fields are numpy arrays.  Both the CUDA library binding and the CPU oracle
+consume the same dicts and arrays, each with its own marshalling.
+
+The workloads stand in for the paper's test problems (natural convection in a
+square porous cavity, Sec. 4.2 and its Table 2; a porous Poiseuille channel
+driven by a body force, the flow part of Sec. 4.1).  The paper uses no dataset:
+every workload is an analytic problem statement, so nothing here is sampled
+from external data.
+
+Side order everywhere is W, E, S, N (x = 0, x = nx - 1, y = 0, y = ny - 1).
+Boundary kinds: "periodic", "dirichlet" (no-slip, prescribed T), "adiabatic"
+(no-slip, zero normal temperature gradient).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+NAN = float("nan")
+
+SIDES = ("W", "E", "S", "N")
+BC_KINDS = ("periodic", "dirichlet", "adiabatic")
+
+_DEFAULTS = dict(
+    nx=32, ny=32,
+    bc=("dirichlet", "dirichlet", "adiabatic", "adiabatic"),
+    forchheimer=1, da_infinite=0,
+    Ra=1e3, Pr=1.0, Da=1e-2, J=1.0, eps=0.6, sigma=1.0, Ma=0.1,
+    tau_f=1.0, tau_T=1.0,
+    Th=1.0, Tc=0.0, T_init=0.5, rho0=1.0, Q=0.0, ax=0.0, ay=0.0,
+    L=NAN, nu=NAN, alpha_e=NAN, gbeta=NAN, A=NAN, B=NAN, K=NAN,
+    T_bc=None, u_bc=((0.0, 0.0), (0.0, 0.0), (0.0, 0.0), (0.0, 0.0)),
+)
+
+
+def problem(**kw) -> dict:
+    """A full problem statement with the paper's defaults (Sec. 4: rho0 = 1,
+    J = 1, sigma = 1, tau_f = tau_T = 1, Ma = 0.1) and the cavity boundary
+    set (hot W wall, cold E wall, adiabatic S and N walls, no slip)."""
+    unknown = set(kw) - set(_DEFAULTS)
+    if unknown:
+        raise KeyError(f"unknown problem keys: {sorted(unknown)}")
+    p = dict(_DEFAULTS)
+    p.update(kw)
+    p["bc"] = tuple(p["bc"])
+    for b in p["bc"]:
+        if b not in BC_KINDS:
+            raise ValueError(f"boundary kind {b!r} not in {BC_KINDS}")
+    if p["T_bc"] is None:
+        p["T_bc"] = (p["Th"], p["Tc"], p["Th"], p["Tc"])
+    p["T_bc"] = tuple(float(v) for v in p["T_bc"])
+    p["u_bc"] = tuple(tuple(float(c) for c in v) for v in p["u_bc"])
+    return p
+
+
+def cavity(n: int, Ra: float, Da: float, eps: float, Pr: float = 1.0, **kw) -> dict:
+    """Square porous cavity of Sec. 4.2 (Table 2 family): n x n nodes,
+    wall nodes included, left wall hot (Th = 1), right wall cold (Tc = 0),
+    adiabatic top and bottom, no slip everywhere, u = 0 and T = 0.5 at t = 0."""
+    return problem(nx=n, ny=n, Ra=Ra, Da=Da, eps=eps, Pr=Pr, **kw)
+
+
+def poiseuille(nx: int = 8, ny: int = 64, G: float = 1e-5, eps: float = 0.5,
+               Da: float = 1e-3, nu: float = 1.0 / 6.0, A: float = 0.0,
+               forchheimer: int = 0, **kw) -> dict:
+    """Porous channel driven by a body force a = (G, 0): periodic in x,
+    no-slip walls at y = 0 and y = ny - 1, channel height H = ny - 1 used as
+    the length in Da = K / H^2.  Temperature uniform at T0 (no buoyancy)."""
+    return problem(nx=nx, ny=ny, bc=("periodic", "periodic", "dirichlet", "dirichlet"),
+                   eps=eps, Da=Da, nu=nu, A=A, forchheimer=forchheimer, ax=G,
+                   L=float(ny - 1), Th=0.5, Tc=0.5, T_init=0.5, gbeta=0.0,
+                   T_bc=(0.5, 0.5, 0.5, 0.5), alpha_e=nu, **kw)
+
+
+# --------------------------------------------------------------- configs
+# The measured configurations: sizes, groups and step counts of the paper's
+# porous-cavity family, scaled up to GB300-sized lattices.
+
+CONFIG_FP64_CAVITY = dict(name="cavity32_fp64", n=32, Ra=1e3, Da=1e-2, eps=0.6, steps=20_000,
+                          precision="f64")
+CONFIG_FP32_CAVITY = dict(name="cavity2048_fp32", n=2048, Ra=1e6, Da=1e-4, eps=0.4,
+                          steps=100_000, precision="f32")
+CONFIG_FP32_ORACLE = dict(name="cavity256_fp32", n=256, Ra=1e6, Da=1e-4, eps=0.4,
+                          steps=100_000, precision="f32")
+CONFIG_FP16_CAVITY = dict(name="cavity8192_fp16", n=8192, Ra=1e5, Da=1e-3, eps=0.6,
+                          steps=2_000, precision="f16")
+
+
+def config_problem(cfg: dict, n: int | None = None) -> dict:
+    return cavity(n or cfg["n"], cfg["Ra"], cfg["Da"], cfg["eps"])
+
+
+# --------------------------------------------------------------- fields
+
+def uniform_fields(p: dict):
+    """T = T_init, u = 0 on every node, as float64 [ny][nx] arrays."""
+    shape = (p["ny"], p["nx"])
+    return (np.full(shape, p["T_init"]), np.zeros(shape), np.zeros(shape))
+
+
+def random_fields(p: dict, seed: int, amp_u: float = 1e-3, amp_T: float = 0.2):
+    """Seeded smooth-ish random T and u fields (for single-step checks):
+    T = T_init + amp_T * noise, u = amp_u * noise, noise ~ U(-1, 1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (p["ny"], p["nx"])
+    T = p["T_init"] + amp_T * rng.uniform(-1.0, 1.0, shape)
+    ux = amp_u * rng.uniform(-1.0, 1.0, shape)
+    uy = amp_u * rng.uniform(-1.0, 1.0, shape)
+    return T, ux, uy
+
+
+def gaussian_random_field(n: int, corr: float = 16.0, seed: int = 1,
+                          lo: float = 0.3, hi: float = 0.9) -> np.ndarray:
+    """Porosity field: white N(0,1) noise on an n x n periodic grid, filtered
+    in Fourier space by a Gaussian of width corr cells, renormalised to zero
+    mean and unit variance, then mapped into [lo, hi] through the normal CDF."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    z = rng.standard_normal((n, n))
+    k = np.fft.fftfreq(n) * 2.0 * math.pi
+    kx, ky = np.meshgrid(k, k, indexing="xy")
+    filt = np.exp(-0.5 * (kx ** 2 + ky ** 2) * corr ** 2)
+    z = np.real(np.fft.ifft2(np.fft.fft2(z) * filt))
+    z = (z - z.mean()) / z.std()
+    phi = 0.5 * (1.0 + np.vectorize(math.erf)(z / math.sqrt(2.0)))
+    return lo + (hi - lo) * phi
+
+
+def batch_cavities(count: int = 512, seed: int = 20150511,
+                   sizes=(64, 96, 128, 192, 256, 384, 512)) -> list[dict]:
+    """Independent cavities: size uniform over `sizes`, Ra log-uniform in
+    [1e3, 1e6], Da log-uniform in [1e-6, 1e-2], eps uniform in [0.3, 0.9]
+    (drawn in that order per cavity)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        n = int(sizes[rng.integers(len(sizes))])
+        Ra = 10.0 ** rng.uniform(3.0, 6.0)
+        Da = 10.0 ** rng.uniform(-6.0, -2.0)
+        eps = rng.uniform(0.3, 0.9)
+        out.append(cavity(n, Ra, Da, eps))
+    return out
