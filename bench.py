@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Throughput of the fused collide-and-stream step on GB300.
+
+Workload: natural convection in a 2048 x 2048 porous cavity (Ra = 1e6,
+Da = 1e-4, eps = 0.4, Pr = 1, J = sigma = 1, tau_f = tau_T = 1, Ma = 0.1),
+FP32 populations, the paper's cavity problem (Sec. 4.2) on a GB300-sized
+lattice.  One benchmark step = one time step of the whole lattice = one launch
+of the fused kernel.  Metric: million lattice updates per second (MLUPS, all
+nodes counted) and the achieved fraction of the measured HBM bandwidth.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank advances its own
+replica of the cavity (the single-cavity step has no exchange that would need
+sharding): weak scaling, value = all ranks' updates / the slowest rank's time.
+``--impl reference`` times the FP64 CPU oracle (the slow reference
+implementation) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="cavity2048_fp32", n=2048, Ra=1e6, Da=1e-4, eps=0.4, Pr=1.0, precision="f32")
+BYTES_PER_CELL = {"f64": 17 * 8 * 2, "f32": 17 * 4 * 2, "f16": 17 * 2 * 2}
+METRIC = "coupled flow+thermal MLUPS and % HBM roofline at 1 GB300 (plain FP32 fused step)"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_f32_2048_traffic.json")
+KERNEL_SOURCES = ("paper_1505_02976_gb300/csrc/lbm_device.cuh", "paper_1505_02976_gb300/csrc/lbm_kernels.cu")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic_per_launch():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    or None when it was taken on a different kernel source."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_launch"])
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- ranks
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Largest value over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ----------------------------------------------------------------- CPU legs
+
+def oracle_mlups(n: int, steps: int) -> tuple[float, float]:
+    """The FP64 CPU oracle as it stands on an n x n cavity with the workload's
+    groups: returns (MLUPS, seconds)."""
+    import oracle
+    from paper_1505_02976_gb300 import workloads as W
+    p = W.cavity(n, WORKLOAD["Ra"], WORKLOAD["Da"], WORKLOAD["eps"], Pr=WORKLOAD["Pr"])
+    o = oracle.Oracle(p)
+    t0 = time.perf_counter()
+    o.run(steps)
+    dt = time.perf_counter() - t0
+    return n * n * steps / dt / 1e6, dt
+
+
+def cpu_baseline_leg() -> dict:
+    n, steps = WORKLOAD["n"], 2
+    v, dt = oracle_mlups(n, steps)
+    return {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{n}x{n} cavity (the benchmark workload), {steps} time steps, "
+                      f"single-threaded FP64 oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n = 512
+    for _ in range(args.warmup):
+        oracle_mlups(n, 1)
+    t0 = time.perf_counter()
+    import oracle
+    from paper_1505_02976_gb300 import workloads as W
+    p = W.cavity(n, WORKLOAD["Ra"], WORKLOAD["Da"], WORKLOAD["eps"], Pr=WORKLOAD["Pr"])
+    o = oracle.Oracle(p)
+    t0 = time.perf_counter()
+    o.run(args.steps)
+    dt = time.perf_counter() - t0
+    v = n * n * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "nx": WORKLOAD["n"], "ny": WORKLOAD["n"],
+                   "Ra": WORKLOAD["Ra"], "Da": WORKLOAD["Da"], "eps": WORKLOAD["eps"],
+                   "Pr": WORKLOAD["Pr"], "reference_sample": f"{n}x{n} cavity, same groups"},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{n}x{n} cavity with the workload's groups, one oracle time "
+                                   f"step per benchmark step, single thread"},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU leg
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1505_02976_gb300 import lbm
+    from paper_1505_02976_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    n, prec = WORKLOAD["n"], WORKLOAD["precision"]
+    p = W.cavity(n, WORKLOAD["Ra"], WORKLOAD["Da"], WORKLOAD["eps"], Pr=WORKLOAD["Pr"])
+    stream = torch.cuda.Stream(device)
+    with torch.cuda.stream(stream):
+        lat = lbm.Lattice(p, prec, device=local, stream=stream)
+    cells = n * n
+
+    # warm-up
+    lat.step(args.warmup)
+    lat.sync()
+
+    # device-timed region: K launches, an event pair around each one
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    clocks = ClockSampler(vis[local] if local < len(vis) else local)
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    clocks.start()
+    time.sleep(0.4)
+    launches0 = lat.launches
+    t_all0.record(stream)
+    for i in range(args.steps):
+        starts[i].record(stream)
+        lat.step(1)
+        ends[i].record(stream)
+    t_all1.record(stream)
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    barrier(world, device)
+    launches = lat.launches - launches0
+    elapsed = t_all0.elapsed_time(t_all1) / 1e3
+    kernel_s = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / 1e3 / args.steps
+    lat.sync()
+    elapsed_max = max_over_ranks(elapsed, world, device)
+    value = world * cells * args.steps / elapsed_max / 1e6
+
+    # end to end through the C ABI with host buffers: H2D of the initial
+    # fields from pinned memory, K steps, D2H of the hot-wall Nusselt number
+    T0 = torch.full((n, n), p["T_init"], dtype=torch.float64).pin_memory()
+    U0 = torch.zeros((n, n), dtype=torch.float64).pin_memory()
+    V0 = torch.zeros((n, n), dtype=torch.float64).pin_memory()
+    nu_local = torch.empty(n, dtype=torch.float64).pin_memory()
+    L = lat.lib
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    rc = L.lbm_set_fields(lat.h, C.c_void_p(T0.data_ptr()), C.c_void_p(U0.data_ptr()),
+                          C.c_void_p(V0.data_ptr()), None, 0)
+    assert rc == 0, lbm.load().lbm_last_error(lat.h)
+    lat.step(args.steps)
+    nu_mean = C.c_double()
+    rc = L.lbm_nusselt(lat.h, 0, C.byref(nu_mean), C.c_void_p(nu_local.data_ptr()))
+    assert rc == 0
+    e2e_s = time.perf_counter() - t0
+    e2e_max = max_over_ranks(e2e_s, world, device)
+    e2e_value = world * cells * args.steps / e2e_max / 1e6
+    h2d = 3 * cells * 8
+    d2h = 8 + n * 8
+
+    peak, peak_kind = measured_peak_gbs()
+    algo_bytes = BYTES_PER_CELL[prec] * cells
+    achieved = algo_bytes / kernel_s / 1e9
+    traffic = ncu_traffic_per_launch()
+
+    out = None
+    if rank == 0:
+        cpu = cpu_baseline_leg() if world == 1 and not args.no_cpu_baseline else None
+        out = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "nx": n, "ny": n, "Ra": WORKLOAD["Ra"],
+                       "Da": WORKLOAD["Da"], "eps": WORKLOAD["eps"], "Pr": WORKLOAD["Pr"],
+                       "storage": prec, "replicas": world,
+                       "l2": "inputs larger than L2: 285 MB of populations read and 285 MB "
+                             "written per step (L2 129 MB), no flush needed"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": algo_bytes,
+                         "kernel_ms": kernel_s * 1e3},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps, "nu_hot": nu_mean.value},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    lat.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

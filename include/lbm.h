@@ -1,0 +1,195 @@
+/*
+ * lbm.h -- C ABI of the GB300 implementation of the fused collide-and-stream
+ * step of the modified lattice BGK model for convection heat transfer in
+ * porous media (Wang, Mi and Guo, arXiv 1505.02976).
+ *
+ * One time step advances two D2Q9 distributions on an nx x ny lattice:
+ *   flow:     f_i(x + c_i, t + 1) = f_i - (f_i - f_i^eq)/tau_f + F_i   (Eq. LBEeq)
+ *   thermal:  g_i(x + c_i, t + 1) = g_i - (g_i - g_i^eq)/tau_T + P_i + Q_i
+ *                                                       (Eqs. LBEHeq, TEqColli)
+ * with the porous equilibrium of Eqs. (EQFIN)-(EQTSHIN), the Guo forcing term
+ * of Eq. (FtermF) carrying the Brinkman-Forchheimer force of Eq. (ForceEq),
+ * the modified thermal equilibrium and sources of Eqs. (TeEDFEQ), (Eq:Tforce),
+ * the local shear-rate and temperature-gradient schemes of Sec. 3.3
+ * (Eqs. ShearEqCom, TeEqCom) and the non-equilibrium extrapolation walls of
+ * Sec. 3.4 (Eqs. NEESVel, TNEESAp, TNEESApGra), all fused into one kernel
+ * launch per step.  Lattice units throughout: dx = dt = 1, c_s^2 = 1/3.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Layout of fields passed in or out: row-major [ny][nx] (x fastest), float64.
+ * Layout of population arrays passed in or out: [9][ny][nx] float64, index i
+ *   in the paper's velocity order (Sec. 3.1): 0 rest, 1 (+1,0), 2 (0,+1),
+ *   3 (-1,0), 4 (0,-1), 5 (+1,+1), 6 (-1,+1), 7 (-1,-1), 8 (+1,-1).
+ * Sides: 0 = W (x = 0), 1 = E (x = nx-1), 2 = S (y = 0), 3 = N (y = ny-1).
+ *   Wall nodes are the outermost nodes; the characteristic length defaults to
+ *   L = nx - 1.
+ * on_device: 0 = the pointers are host memory (the call copies through a
+ *   device staging area and returns after the copy); 1 = the pointers are
+ *   device memory of the handle's device (the call is asynchronous on the
+ *   handle's stream).
+ * Ownership: the caller owns every pointer it passes; nothing is retained
+ *   after a call returns.  The handle owns its device state, which lives in
+ *   the workspace (caller-provided or allocated by lbm_create).
+ * Errors: every entry point returns an lbm_status; no exception or abort
+ *   crosses the ABI.  lbm_last_error() gives a message for the last failure.
+ *   LBM_ERR_NONFINITE is sticky until lbm_set_fields or lbm_set_state.
+ * Threading: a handle must not be used from two threads at once.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_handle lbm_handle;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,          /* bad pointer, size, side or flag */
+    LBM_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+    LBM_ERR_NONFINITE = -3,    /* a NaN/Inf appeared in u or T during a step */
+    LBM_ERR_TIMEOUT = -4,      /* a bounded device-side wait gave up */
+    LBM_ERR_PARAM_RANGE = -5,  /* parameters outside the model's range (Sec. 4) */
+    LBM_ERR_OOM = -6           /* workspace too small or allocation failed */
+} lbm_status;
+
+/* Storage type of the populations.  LBM_F64 computes in FP64, LBM_F32 in
+ * FP32; both store the flow populations f_1..f_8 as they are and the thermal
+ * populations as deviations g_i - w_i sigma T0 from the rest state. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2 } lbm_precision;
+
+/* Boundary kind of one side. */
+typedef enum {
+    LBM_BC_PERIODIC = 0,   /* periodic; the opposite side must be periodic too */
+    LBM_BC_DIRICHLET = 1,  /* no-slip (velocity u_bc) and prescribed T = T_bc */
+    LBM_BC_ADIABATIC = 2   /* no-slip (velocity u_bc) and dT/dn = 0 */
+} lbm_bc;
+
+/* Problem statement, in the paper's dimensionless groups (Sec. 2, Sec. 4).
+ * The fields marked "NaN = derive" are derived when they hold NaN:
+ *   L      = nx - 1
+ *   U      = Ma c_s                       (characteristic velocity, Sec. 4)
+ *   gbeta  = U^2 / ((Th - Tc) L)          (U^2 = g beta dT L)
+ *   nu     = U L sqrt(Pr / Ra)            (Ra, Pr of Sec. 2); when A is given
+ *            instead, nu = c_s^2 (tau_f - A - 1/2) / J
+ *   alpha_e= nu / Pr; when B is given instead, sigma c_s^2 (tau_T - B - 1/2)
+ *   A      = tau_f - 1/2 - J nu / c_s^2   (Eq. EQA&B for J = 1)
+ *   B      = tau_T - 1/2 - alpha_e / (sigma c_s^2)
+ *   K      = Da L^2                       (Sec. 2)
+ * F_eps = 1.75 / sqrt(150 eps^3) (Ergun) when forchheimer = 1, else 0.
+ * T0 = (Th + Tc) / 2 is the buoyancy reference and the thermal rest state;
+ * Th - Tc normalises the Nusselt number. */
+typedef struct {
+    int32_t nx, ny;          /* nodes, wall nodes included; >= 4 across walls */
+    int32_t bc[4];           /* lbm_bc per side W, E, S, N */
+    int32_t forchheimer;     /* 1: Ergun F_eps, 0: no quadratic drag */
+    int32_t da_infinite;     /* 1: K = infinity (no Darcy/Forchheimer drag) */
+    int32_t precision;       /* lbm_precision */
+    int32_t reserved;        /* must be 0 */
+    double Ra, Pr, Da, J, eps, sigma, Ma;
+    double tau_f, tau_T;
+    double Th, Tc, T_init, rho0, Q, ax, ay;
+    double L, nu, alpha_e, gbeta, A, B, K;   /* NaN = derive */
+    double T_bc[4];          /* Dirichlet wall temperature per side */
+    double u_bc[4][2];       /* wall velocity per side */
+} lbm_params;
+
+/* Fill p with the paper's defaults (Sec. 4): the 32 x 32 porous cavity,
+ * hot W wall T = 1, cold E wall T = 0, adiabatic S and N, no slip, rho0 = 1,
+ * J = sigma = 1, tau_f = tau_T = 1, Ma = 0.1, Ra = 1e3, Da = 1e-2,
+ * eps = 0.6, Pr = 1, Forchheimer on, T_init = 0.5, FP32 storage. */
+lbm_status lbm_params_default(lbm_params* p);
+
+/* Derived lattice constants of p, in this order:
+ * L, T0, dT, U, gbeta, nu, nu_e, alpha_e, A, B, K, F_eps (12 doubles).
+ * Returns LBM_ERR_PARAM_RANGE when the parameters are outside the range the
+ * model admits: 0 < eps <= 1, tau > 1/2, A < tau_f - 1/2, B < tau_T - 1/2
+ * (Sec. 4), sigma > 0, rho0 > 0. */
+lbm_status lbm_derived(const lbm_params* p, double out[12]);
+
+/* Bytes of device workspace a handle for p needs (two population buffers,
+ * field staging, reduction scratch, residual snapshot). */
+lbm_status lbm_workspace_size(const lbm_params* p, size_t* bytes);
+
+/* Create a handle.  stream: a cudaStream_t (NULL = the legacy default
+ * stream).  workspace: device memory of at least lbm_workspace_size() bytes
+ * aligned to 256 bytes, owned by the caller and kept alive until
+ * lbm_destroy; NULL = the library allocates it (cudaMalloc) and frees it in
+ * lbm_destroy.  The lattice starts at the uniform rest state
+ * (u = 0, p = 0, T = T_init): call lbm_set_fields to change it. */
+lbm_status lbm_create(const lbm_params* p, void* stream, void* workspace,
+                      size_t workspace_bytes, lbm_handle** out);
+
+void lbm_destroy(lbm_handle* h);
+
+/* Message of the last failure on h (or of the last failed lbm_create when h is
+ * NULL).  Valid until the next call on h. */
+const char* lbm_last_error(const lbm_handle* h);
+
+/* Initialise the state from macroscopic fields: the post-collision
+ * populations become f = f^eq(p = 0, u, S = 0) and
+ * g = g^eq(T, u, p = 0, grad T = 0) (Eqs. EQFIN, TeEDFEQ).  Any of T, ux, uy
+ * may be NULL (T_init, 0, 0).  eps_field must be NULL (a uniform porosity
+ * eps is used).  Resets the step counter and the non-finite flag. */
+lbm_status lbm_set_fields(lbm_handle* h, const double* T, const double* ux,
+                          const double* uy, const double* eps_field,
+                          int on_device);
+
+/* Advance n >= 0 time steps (stream, rebuild walls, collide; one kernel
+ * launch per step).  Asynchronous on the handle's stream.  Returns
+ * LBM_ERR_NONFINITE if an earlier synchronising call saw the flag. */
+lbm_status lbm_step(lbm_handle* h, int64_t n);
+
+/* Wait for the handle's stream; returns LBM_ERR_NONFINITE if any step since
+ * the last reset produced a non-finite velocity or temperature. */
+lbm_status lbm_sync(lbm_handle* h);
+
+/* Macroscopic fields of the current state: the pressure, velocity and
+ * temperature that the next step computes after streaming (Sec. 3.1-3.2);
+ * wall nodes report their boundary state (u_b, T_b, p(x_f)) of Sec. 3.4.
+ * Any output may be NULL.  Host outputs: the call synchronises. */
+lbm_status lbm_moments(lbm_handle* h, double* p, double* ux, double* uy,
+                       double* T, int on_device);
+
+/* Average Nusselt number on one wall (Eq. Eq:AvNuss):
+ * Nu(s) = -L (dT/dn) / (Th - Tc), the derivative along +x (W, E walls) or +y
+ * (S, N walls) taken by the second-order one-sided difference from the wall
+ * node inward; the mean is the trapezoid rule over the wall's nodes divided
+ * by (number of nodes - 1).  Temperatures are taken in FP64 from the stored
+ * populations.  nu_local (NULL allowed) receives ny (W, E) or nx (S, N)
+ * values, in host memory.  Synchronises. */
+lbm_status lbm_nusselt(lbm_handle* h, int side, double* nu_mean, double* nu_local);
+
+/* Steady-state criterion of Sec. 4 against the snapshot taken by the
+ * previous lbm_residual call (or lbm_set_fields):
+ *   res_u = sum |u - u_old|_2 / sum |u|_2,  res_T = sum |T - T_old| / sum |T|,
+ * reduced in FP64 in a fixed order (deterministic), then the snapshot is
+ * replaced by the current fields.  Synchronises. */
+lbm_status lbm_residual(lbm_handle* h, double* res_u, double* res_T);
+
+/* The post-collision populations of the last step as float64 [9][ny][nx]
+ * arrays, g absolute (not as a deviation).  f_0 is not stored by the GPU
+ * path (no moment reads it: p uses sum_{i!=0} f_i, Sec. 3.1) and is
+ * reported as NaN. */
+lbm_status lbm_get_state(lbm_handle* h, double* f, double* g, int on_device);
+
+/* Load post-collision populations (layout of lbm_get_state; f_0 ignored).
+ * Resets the non-finite flag; keeps the step counter. */
+lbm_status lbm_set_state(lbm_handle* h, const double* f, const double* g, int on_device);
+
+/* Steps completed since the last lbm_set_fields. */
+int64_t lbm_steps_done(const lbm_handle* h);
+
+/* Number of step-kernel launches issued by this handle so far. */
+int64_t lbm_kernel_launches(const lbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

@@ -192,6 +192,19 @@ class Oracle:
             raise ValueError(f"oracle rejected the problem (code {rc})")
         self.steps = 0
 
+    @classmethod
+    def from_state(cls, p: dict, f, g, eps_field=None):
+        """An oracle lattice holding the given post-collision populations."""
+        o = cls.__new__(cls)
+        o.p = dict(p)
+        o.s = problem_struct(p)
+        o.nx, o.ny = int(p["nx"]), int(p["ny"])
+        o.eps_field = _c64(eps_field)
+        o.steps = 0
+        derived(p)  # validates the problem
+        o.set_state(f, g)
+        return o
+
     def set_state(self, f, g):
         self.f = np.ascontiguousarray(f, dtype=np.float64).copy()
         self.g = np.ascontiguousarray(g, dtype=np.float64).copy()

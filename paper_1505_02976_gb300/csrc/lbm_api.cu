@@ -1,0 +1,505 @@
+// lbm_api.cu -- the C ABI declared in include/lbm.h: parameter derivation,
+// workspace layout, launches and error handling.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <type_traits>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+namespace {
+
+constexpr double kCs2 = 1.0 / 3.0;
+constexpr double kW0 = 4.0 / 9.0;
+
+struct Derived {
+    double L, T0, dT, U, gbeta, nu, nu_e, alpha_e, A, B, K, Feps;
+};
+
+thread_local std::string g_create_error;
+
+bool isnan_(double v) { return v != v; }
+
+// Lattice constants from the problem statement (Sec. 2, Sec. 4, Eq. EQA&B,
+// Eq. Therdiff, Appendix A): see the table in include/lbm.h.
+lbm_status derive(const lbm_params* p, Derived* d, std::string* why) {
+    d->L = isnan_(p->L) ? double(p->nx - 1) : p->L;
+    d->T0 = 0.5 * (p->Th + p->Tc);
+    d->dT = p->Th - p->Tc;
+    d->U = p->Ma * sqrt(kCs2);
+    d->gbeta = isnan_(p->gbeta) ? d->U * d->U / (d->dT * d->L) : p->gbeta;
+    if (!isnan_(p->nu)) d->nu = p->nu;
+    else if (!isnan_(p->A)) d->nu = kCs2 * (p->tau_f - p->A - 0.5) / p->J;
+    else d->nu = d->U * d->L * sqrt(p->Pr / p->Ra);
+    d->nu_e = p->J * d->nu;
+    if (!isnan_(p->alpha_e)) d->alpha_e = p->alpha_e;
+    else if (!isnan_(p->B)) d->alpha_e = p->sigma * kCs2 * (p->tau_T - p->B - 0.5);
+    else d->alpha_e = d->nu / p->Pr;
+    d->A = isnan_(p->A) ? p->tau_f - 0.5 - d->nu_e / kCs2 : p->A;
+    d->B = isnan_(p->B) ? p->tau_T - 0.5 - d->alpha_e / (p->sigma * kCs2) : p->B;
+    d->K = p->da_infinite ? INFINITY : (isnan_(p->K) ? p->Da * d->L * d->L : p->K);
+    d->Feps = p->forchheimer ? 1.75 / sqrt(150.0 * p->eps * p->eps * p->eps) : 0.0;
+    auto bad = [&](const char* m) {
+        if (why) *why = m;
+        return LBM_ERR_PARAM_RANGE;
+    };
+    if (!(p->eps > 0.0 && p->eps <= 1.0)) return bad("porosity eps must lie in (0, 1]");
+    if (!(p->tau_f > 0.5 && p->tau_T > 0.5)) return bad("relaxation times must exceed 1/2");
+    if (!(d->A < p->tau_f - 0.5)) return bad("A must be below tau_f - 1/2 (positive viscosity)");
+    if (!(d->B < p->tau_T - 0.5)) return bad("B must be below tau_T - 1/2 (positive diffusivity)");
+    if (!(p->sigma > 0.0 && p->rho0 > 0.0)) return bad("sigma and rho0 must be positive");
+    if (!(isfinite(d->gbeta) && isfinite(d->nu) && isfinite(d->alpha_e) && isfinite(d->T0)))
+        return bad("derived constants are not finite (check Ra, Pr, Ma, Th - Tc)");
+    return LBM_OK;
+}
+
+lbm_status check_shape(const lbm_params* p, std::string* why) {
+    for (int s = 0; s < 4; ++s)
+        if (p->bc[s] < 0 || p->bc[s] > 2) { *why = "unknown boundary kind"; return LBM_ERR_ARG; }
+    if ((p->bc[0] == LBM_BC_PERIODIC) != (p->bc[1] == LBM_BC_PERIODIC) ||
+        (p->bc[2] == LBM_BC_PERIODIC) != (p->bc[3] == LBM_BC_PERIODIC)) {
+        *why = "a periodic side needs a periodic opposite side";
+        return LBM_ERR_ARG;
+    }
+    if (p->nx < 1 || p->ny < 1 || p->ny > 65535 || p->nx > (1 << 24)) {
+        *why = "lattice size out of range (1 <= nx, 1 <= ny <= 65535)";
+        return LBM_ERR_ARG;
+    }
+    if ((p->bc[0] != LBM_BC_PERIODIC && p->nx < 4) || (p->bc[2] != LBM_BC_PERIODIC && p->ny < 4)) {
+        *why = "a walled direction needs at least 4 nodes";
+        return LBM_ERR_ARG;
+    }
+    if (p->precision < LBM_F64 || p->precision > LBM_F16 || p->reserved != 0) {
+        *why = "unknown precision";
+        return LBM_ERR_ARG;
+    }
+    return LBM_OK;
+}
+
+size_t elem_size(int precision) {
+    return precision == LBM_F64 ? 8 : (precision == LBM_F32 ? 4 : 2);
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Layout {
+    int pitch;
+    size_t plane_elems, buf_bytes;
+    size_t off_buf[2], off_fields, off_snap, off_nu, off_partial, off_out, off_flag, total;
+};
+
+Layout layout(const lbm_params* p) {
+    Layout L;
+    const size_t es = elem_size(p->precision);
+    const size_t row = ((size_t)p->nx * es + 127) / 128 * 128;  // 128-byte rows
+    L.pitch = int(row / es);
+    L.plane_elems = (size_t)L.pitch * p->ny;
+    L.buf_bytes = align256(L.plane_elems * es * lbm::NPLANES);
+    const size_t N = (size_t)p->nx * p->ny;
+    size_t o = 0;
+    L.off_buf[0] = o; o += L.buf_bytes;
+    L.off_buf[1] = o; o += L.buf_bytes;
+    L.off_fields = o; o += align256(4 * N * sizeof(double));
+    L.off_snap = o; o += align256(3 * N * sizeof(double));
+    L.off_nu = o; o += align256((size_t)(p->nx > p->ny ? p->nx : p->ny) * sizeof(double));
+    L.off_partial = o; o += align256((size_t)lbm::residual_blocks(p->nx, p->ny) * 4 * sizeof(double));
+    L.off_out = o; o += 256;
+    L.off_flag = o; o += 256;
+    L.total = o;
+    return L;
+}
+
+template <class R>
+lbm::KConst<R> make_kconst(const lbm_params* p, const Derived& d, const Layout& L, int* flag) {
+    lbm::KConst<R> k;
+    memset(&k, 0, sizeof(k));
+    k.nx = p->nx;
+    k.ny = p->ny;
+    k.pitch = L.pitch;
+    for (int s = 0; s < 4; ++s) k.bc[s] = p->bc[s];
+    k.plane = (long long)L.plane_elems;
+    const double eps = p->eps;
+    const double nuK = isinf(d.K) ? 0.0 : d.nu / d.K;
+    const double FK = isinf(d.K) ? 0.0 : d.Feps / sqrt(d.K);
+    const double c0 = 0.5 * (1.0 + eps * 0.5 * nuK);
+    const double c1 = eps * 0.5 * FK;
+    k.rho0 = R(p->rho0);
+    k.eps = R(eps);
+    k.inv_eps = R(1.0 / eps);
+    k.sigma = R(p->sigma);
+    k.inv_sigma = R(1.0 / p->sigma);
+    k.omf = R(1.0 - 1.0 / p->tau_f);
+    k.omT = R(1.0 - 1.0 / p->tau_T);
+    k.tau_f = R(p->tau_f);
+    k.kf = R(1.0 - 0.5 / p->tau_f);
+    k.kT = R(1.0 - 0.5 / p->tau_T);
+    k.A = R(d.A);
+    k.B = R(d.B);
+    k.T0 = R(d.T0);
+    k.gbeta = R(d.gbeta);
+    k.ax = R(p->ax);
+    k.ay = R(p->ay);
+    k.Q = R(p->Q);
+    k.e_nuK = R(eps * nuK);
+    k.e_FK = R(eps * FK);
+    k.c0 = R(c0);
+    k.c0sq = R(c0 * c0);
+    k.c1 = R(c1);
+    k.p_pref = R(kCs2 / (eps * (1.0 - kW0)));
+    k.invD = R(1.0 / (kCs2 * p->rho0 * (d.A - p->tau_f)));
+    k.a_const = R(kCs2 * p->sigma * (d.B - p->tau_T));
+    k.bcoef = R(0.5 * (1.0 / eps - 1.0 / p->sigma));
+    k.sT0 = R(p->sigma * d.T0);
+    for (int s = 0; s < 4; ++s) {
+        k.T_bc[s] = R(p->T_bc[s]);
+        k.u_bc[s][0] = R(p->u_bc[s][0]);
+        k.u_bc[s][1] = R(p->u_bc[s][1]);
+    }
+    k.scale = p->precision == LBM_F16 ? ldexpf(1.0f, -10) : 1.0f;
+    k.flag = flag;
+    return k;
+}
+
+}  // namespace
+
+struct lbm_handle {
+    lbm_params prm;
+    Derived d;
+    Layout L;
+    cudaStream_t stream;
+    char* ws;
+    bool owns_ws;
+    int cur;
+    int64_t steps, launches;
+    bool nonfinite;
+    lbm::KConst<double> k64;
+    lbm::KConst<float> k32;
+    lbm::DiagConst diag;
+    std::string err;
+
+    void* buf(int i) const { return ws + L.off_buf[i]; }
+    double* fields() const { return (double*)(ws + L.off_fields); }
+    double* snap() const { return (double*)(ws + L.off_snap); }
+    double* nu() const { return (double*)(ws + L.off_nu); }
+    double* partial() const { return (double*)(ws + L.off_partial); }
+    double* out() const { return (double*)(ws + L.off_out); }
+    int* flag() const { return (int*)(ws + L.off_flag); }
+    size_t N() const { return (size_t)prm.nx * prm.ny; }
+};
+
+namespace {
+
+lbm_status fail(lbm_handle* h, lbm_status s, const std::string& m) {
+    if (h) h->err = m;
+    else g_create_error = m;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_handle* h, cudaError_t e, const char* what) {
+    return fail(h, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(h, call, what)                                   \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, (what)); \
+    } while (0)
+
+// Dispatch on the storage precision.
+template <class F>
+cudaError_t dispatch(lbm_handle* h, F&& fn) {
+    switch (h->prm.precision) {
+    case LBM_F64: return fn(h->k64, (double*)nullptr);
+    case LBM_F32: return fn(h->k32, (float*)nullptr);
+    default: return fn(h->k32, (__half*)nullptr);
+    }
+}
+
+lbm_status copy_in(lbm_handle* h, double* dst, const double* src, int on_device) {
+    const size_t bytes = h->N() * sizeof(double);
+    LBM_CUDA(h, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                h->stream), "copy of an input field");
+    return LBM_OK;
+}
+
+lbm_status reset_snapshot(lbm_handle* h) {
+    cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        return lbm::launch_residual(k, (const S*)h->buf(h->cur), h->snap(), h->partial(), h->out(), h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "residual snapshot");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_params_default(lbm_params* p) {
+    if (!p) return LBM_ERR_ARG;
+    memset(p, 0, sizeof(*p));
+    p->nx = p->ny = 32;
+    p->bc[0] = LBM_BC_DIRICHLET;
+    p->bc[1] = LBM_BC_DIRICHLET;
+    p->bc[2] = LBM_BC_ADIABATIC;
+    p->bc[3] = LBM_BC_ADIABATIC;
+    p->forchheimer = 1;
+    p->da_infinite = 0;
+    p->precision = LBM_F32;
+    p->Ra = 1e3; p->Pr = 1.0; p->Da = 1e-2; p->J = 1.0; p->eps = 0.6; p->sigma = 1.0; p->Ma = 0.1;
+    p->tau_f = 1.0; p->tau_T = 1.0;
+    p->Th = 1.0; p->Tc = 0.0; p->T_init = 0.5; p->rho0 = 1.0; p->Q = 0.0; p->ax = 0.0; p->ay = 0.0;
+    p->L = p->nu = p->alpha_e = p->gbeta = p->A = p->B = p->K = NAN;
+    p->T_bc[0] = 1.0; p->T_bc[1] = 0.0; p->T_bc[2] = 1.0; p->T_bc[3] = 0.0;
+    return LBM_OK;
+}
+
+lbm_status lbm_derived(const lbm_params* p, double out[12]) {
+    if (!p || !out) return LBM_ERR_ARG;
+    Derived d;
+    std::string why;
+    lbm_status s = derive(p, &d, &why);
+    const double v[12] = {d.L, d.T0, d.dT, d.U, d.gbeta, d.nu, d.nu_e, d.alpha_e, d.A, d.B, d.K, d.Feps};
+    memcpy(out, v, sizeof(v));
+    return s;
+}
+
+lbm_status lbm_workspace_size(const lbm_params* p, size_t* bytes) {
+    if (!p || !bytes) return LBM_ERR_ARG;
+    std::string why;
+    lbm_status s = check_shape(p, &why);
+    if (s != LBM_OK) return fail(nullptr, s, why);
+    *bytes = layout(p).total;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_params* p, void* stream, void* workspace, size_t workspace_bytes,
+                      lbm_handle** out) {
+    if (!p || !out) return fail(nullptr, LBM_ERR_ARG, "null argument");
+    *out = nullptr;
+    std::string why;
+    lbm_status s = check_shape(p, &why);
+    if (s != LBM_OK) return fail(nullptr, s, why);
+    Derived d;
+    s = derive(p, &d, &why);
+    if (s != LBM_OK) return fail(nullptr, s, why);
+    const Layout L = layout(p);
+    if (workspace && (workspace_bytes < L.total || ((uintptr_t)workspace & 255)))
+        return fail(nullptr, LBM_ERR_OOM, "workspace too small or not 256-byte aligned");
+    lbm_handle* h = new (std::nothrow) lbm_handle();
+    if (!h) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    h->prm = *p;
+    h->d = d;
+    h->L = L;
+    h->stream = (cudaStream_t)stream;
+    h->owns_ws = workspace == nullptr;
+    h->ws = (char*)workspace;
+    if (h->owns_ws) {
+        cudaError_t e = cudaMalloc((void**)&h->ws, L.total);
+        if (e != cudaSuccess) {
+            delete h;
+            return fail(nullptr, LBM_ERR_OOM, std::string("cudaMalloc of the workspace: ") + cudaGetErrorString(e));
+        }
+    }
+    h->cur = 0;
+    h->steps = h->launches = 0;
+    h->nonfinite = false;
+    h->k64 = make_kconst<double>(p, d, L, h->flag());
+    h->k32 = make_kconst<float>(p, d, L, h->flag());
+    h->diag.T0 = d.T0;
+    h->diag.inv_sigma = 1.0 / p->sigma;
+    h->diag.Q = p->Q;
+    h->diag.L = d.L;
+    h->diag.dT = d.dT;
+    for (int q = 0; q < 4; ++q) h->diag.T_bc[q] = p->T_bc[q];
+    s = lbm_set_fields(h, nullptr, nullptr, nullptr, nullptr, 1);
+    if (s != LBM_OK) {
+        g_create_error = h->err;
+        lbm_destroy(h);
+        return s;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle* h) {
+    if (!h) return;
+    if (h->owns_ws && h->ws) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->ws);
+    }
+    delete h;
+}
+
+const char* lbm_last_error(const lbm_handle* h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+lbm_status lbm_set_fields(lbm_handle* h, const double* T, const double* ux, const double* uy,
+                          const double* eps_field, int on_device) {
+    if (!h) return LBM_ERR_ARG;
+    if (eps_field) return fail(h, LBM_ERR_ARG, "a porosity field is not supported by this entry point");
+    double* F = h->fields();
+    const size_t N = h->N();
+    const double* dT = nullptr;
+    const double* dux = nullptr;
+    const double* duy = nullptr;
+    lbm_status s;
+    if (T) { if ((s = copy_in(h, F, T, on_device)) != LBM_OK) return s; dT = F; }
+    if (ux) { if ((s = copy_in(h, F + N, ux, on_device)) != LBM_OK) return s; dux = F + N; }
+    if (uy) { if ((s = copy_in(h, F + 2 * N, uy, on_device)) != LBM_OK) return s; duy = F + 2 * N; }
+    h->cur = 0;
+    cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        return lbm::launch_init(k, (S*)h->buf(0), dT, dux, duy, h->prm.T_init, h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
+    LBM_CUDA(h, cudaMemsetAsync(h->flag(), 0, sizeof(int), h->stream), "flag reset");
+    if ((s = reset_snapshot(h)) != LBM_OK) return s;
+    if (!on_device) LBM_CUDA(h, cudaStreamSynchronize(h->stream), "set_fields");
+    h->steps = 0;
+    h->nonfinite = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_handle* h, int64_t n) {
+    if (!h || n < 0) return h ? fail(h, LBM_ERR_ARG, "negative step count") : LBM_ERR_ARG;
+    if (h->nonfinite) return fail(h, LBM_ERR_NONFINITE, "non-finite velocity or temperature");
+    for (int64_t i = 0; i < n; ++i) {
+        const int src = h->cur, dst = 1 - h->cur;
+        cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            return lbm::launch_step(k, (const S*)h->buf(src), (S*)h->buf(dst), h->stream);
+        });
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+        h->cur = dst;
+        ++h->steps;
+        ++h->launches;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_handle* h) {
+    if (!h) return LBM_ERR_ARG;
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "stream synchronise");
+    int flag = 0;
+    LBM_CUDA(h, cudaMemcpy(&flag, h->flag(), sizeof(int), cudaMemcpyDeviceToHost), "flag read");
+    if (flag) h->nonfinite = true;
+    if (h->nonfinite) return fail(h, LBM_ERR_NONFINITE, "non-finite velocity or temperature");
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_handle* h, double* p, double* ux, double* uy, double* T, int on_device) {
+    if (!h) return LBM_ERR_ARG;
+    double* F = h->fields();
+    const size_t N = h->N();
+    cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        return lbm::launch_moments(k, (const S*)h->buf(h->cur), F, F + N, F + 2 * N, F + 3 * N, h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
+    double* outs[4] = {p, ux, uy, T};
+    for (int q = 0; q < 4; ++q)
+        if (outs[q])
+            LBM_CUDA(h, cudaMemcpyAsync(outs[q], F + q * N, N * sizeof(double),
+                                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream),
+                     "copy of a moment field");
+    if (!on_device) LBM_CUDA(h, cudaStreamSynchronize(h->stream), "moments");
+    return LBM_OK;
+}
+
+lbm_status lbm_nusselt(lbm_handle* h, int side, double* nu_mean, double* nu_local) {
+    if (!h) return LBM_ERR_ARG;
+    if (side < 0 || side > 3 || !nu_mean) return fail(h, LBM_ERR_ARG, "bad side or null output");
+    const int n = side <= 1 ? h->prm.ny : h->prm.nx;
+    const int across = side <= 1 ? h->prm.nx : h->prm.ny;
+    if (across < 3) return fail(h, LBM_ERR_ARG, "the one-sided difference needs 3 nodes");
+    cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        return lbm::launch_nusselt(k, h->diag, (const S*)h->buf(h->cur), side, h->nu(), h->out(), h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "nusselt kernels");
+    LBM_CUDA(h, cudaMemcpyAsync(nu_mean, h->out(), sizeof(double), cudaMemcpyDeviceToHost, h->stream), "nusselt copy");
+    if (nu_local)
+        LBM_CUDA(h, cudaMemcpyAsync(nu_local, h->nu(), n * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                 "nusselt copy");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "nusselt");
+    return LBM_OK;
+}
+
+lbm_status lbm_residual(lbm_handle* h, double* res_u, double* res_T) {
+    if (!h || !res_u || !res_T) return h ? fail(h, LBM_ERR_ARG, "null output") : LBM_ERR_ARG;
+    lbm_status s = reset_snapshot(h);
+    if (s != LBM_OK) return s;
+    double v[4];
+    LBM_CUDA(h, cudaMemcpyAsync(v, h->out(), sizeof(v), cudaMemcpyDeviceToHost, h->stream), "residual copy");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "residual");
+    *res_u = v[0] / v[1];
+    *res_T = v[2] / v[3];
+    return LBM_OK;
+}
+
+lbm_status lbm_get_state(lbm_handle* h, double* f, double* g, int on_device) {
+    if (!h || !f || !g) return h ? fail(h, LBM_ERR_ARG, "null output") : LBM_ERR_ARG;
+    const size_t bytes = 9 * h->N() * sizeof(double);
+    double* df = f;
+    double* dg = g;
+    double* tmp = nullptr;
+    if (!on_device) {
+        LBM_CUDA(h, cudaMallocAsync((void**)&tmp, 2 * bytes, h->stream), "state staging");
+        df = tmp;
+        dg = tmp + 9 * h->N();
+    }
+    cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        return lbm::launch_get_state(k, (const S*)h->buf(h->cur), df, dg, h->prm.sigma * h->d.T0, h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_state kernel");
+    if (!on_device) {
+        LBM_CUDA(h, cudaMemcpyAsync(f, df, bytes, cudaMemcpyDeviceToHost, h->stream), "state copy");
+        LBM_CUDA(h, cudaMemcpyAsync(g, dg, bytes, cudaMemcpyDeviceToHost, h->stream), "state copy");
+        LBM_CUDA(h, cudaFreeAsync(tmp, h->stream), "state staging");
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream), "get_state");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_handle* h, const double* f, const double* g, int on_device) {
+    if (!h || !f || !g) return h ? fail(h, LBM_ERR_ARG, "null input") : LBM_ERR_ARG;
+    const size_t bytes = 9 * h->N() * sizeof(double);
+    const double* df = f;
+    const double* dg = g;
+    double* tmp = nullptr;
+    if (!on_device) {
+        LBM_CUDA(h, cudaMallocAsync((void**)&tmp, 2 * bytes, h->stream), "state staging");
+        LBM_CUDA(h, cudaMemcpyAsync(tmp, f, bytes, cudaMemcpyHostToDevice, h->stream), "state copy");
+        LBM_CUDA(h, cudaMemcpyAsync(tmp + 9 * h->N(), g, bytes, cudaMemcpyHostToDevice, h->stream), "state copy");
+        df = tmp;
+        dg = tmp + 9 * h->N();
+    }
+    cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        return lbm::launch_set_state(k, (S*)h->buf(h->cur), df, dg, h->prm.sigma * h->d.T0, h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state kernel");
+    LBM_CUDA(h, cudaMemsetAsync(h->flag(), 0, sizeof(int), h->stream), "flag reset");
+    if (!on_device) {
+        LBM_CUDA(h, cudaFreeAsync(tmp, h->stream), "state staging");
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream), "set_state");
+    }
+    h->nonfinite = false;
+    return LBM_OK;
+}
+
+int64_t lbm_steps_done(const lbm_handle* h) { return h ? h->steps : -1; }
+
+int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,306 @@
+// lbm_device.cuh -- per-node arithmetic of the modified LBGK step (device side).
+//
+// One node of one time step, in the order the paper defines it:
+//   pull-stream f_i, g_i from x - c_i                      (Eq. LBEeq, streaming of Sec. 3.2)
+//   T from sigma T = sum g + Q/2                            (Sec. 3.2)
+//   G = g beta (T - T0) j + a; v; u from the quadratic solve (Sec. 3.1)
+//   F = -eps nu/K u - eps F_eps/sqrt(K) |u| u + eps G        (Eq. ForceEq)
+//   p from sum_{i!=0} f_i, F_0 and s_0                       (Sec. 3.1, Appendix A)
+//   S from the non-equilibrium second moment                 (Eq. ShearEqCom)
+//   grad T from the 2x2 system M grad T = N                  (Eqs. TeEqCom-MatrN)
+//   collide f and g                                          (Eqs. LBEeq, TEqColli)
+// Wall nodes are rebuilt by non-equilibrium extrapolation from x_f (Sec. 3.4).
+//
+// The tensor contractions are expanded in closed form for D2Q9 (c_s^2 = 1/3):
+//   s_i  = w_i [3 cu + 4.5 cu^2/eps - 1.5 |u|^2/eps]
+//   r_i  = 1.5 w_i A [cx^2 Sxx + 2 cx cy Sxy + cy^2 Syy - (Sxx + Syy)/3]
+//   F_i  = w_i rho0 (1 - 1/2tau_f) [3 cF + 9 cu cF/eps - 3 u.F/eps]
+//   P_i  = w_i (1 - 1/2tau_T) [3 c.(T F + eps p grad T/rho0) + 3 (1/eps - 1/sigma) cu (u.grad T)]
+//   Q_i  = w_i (1 - 1/2tau_T) (1 + 3 cu/sigma) Q
+// and the moments the local schemes need use the closed-form equilibrium
+// moments (Appendix A, Eq. EqZEqu; Sec. 3.2, Eq. MeOtEq):
+//   sum c c f^{e(0)} = eps p I + rho0 u u / eps,  sum c g^{e(0)} = T u.
+//
+// Storage: flow populations f_1..f_8 as they are (f_0 is never read: p uses
+// sum_{i!=0} f_i, u uses sum c_i f_i, S uses sum c c (f - f^{e(0)})), thermal
+// populations as deviations h_i = g_i - w_i sigma T0 from the rest state.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// D2Q9 in the paper's order (Sec. 3.1).
+__host__ __device__ constexpr int cx_of(int i) {
+    return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int cy_of(int i) {
+    return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
+template <class R>
+__host__ __device__ constexpr R w_of(int i) {
+    return i == 0 ? R(4) / R(9) : (i <= 4 ? R(1) / R(9) : R(1) / R(36));
+}
+
+enum : int { BC_PERIODIC = 0, BC_DIRICHLET = 1, BC_ADIABATIC = 2 };
+enum : int { SW = 0, SE = 1, SS = 2, SN = 3 };
+
+// Constants of one run in the compute type R (filled on the host).
+template <class R>
+struct KConst {
+    int nx, ny, pitch;     // pitch: elements per stored row
+    int bc[4];
+    long long plane;       // elements per stored plane (ny * pitch)
+    R rho0, eps, inv_eps, sigma, inv_sigma;
+    R omf, omT;            // 1 - 1/tau
+    R tau_f, kf, kT;       // kf, kT = 1 - 1/(2 tau)
+    R A, B, T0, gbeta, ax, ay, Q;
+    R e_nuK, e_FK;         // eps nu / K, eps F_eps / sqrt(K)
+    R c0, c0sq, c1;
+    R p_pref;              // c_s^2 / (eps (1 - w_0)) = 3 / (5 eps)
+    R invD;                // 1 / (c_s^2 rho0 (A - tau_f))
+    R a_const;             // c_s^2 sigma (B - tau_T)
+    R bcoef;               // (1/eps - 1/sigma) / 2
+    R sT0;                 // sigma T0
+    R T_bc[4];
+    R u_bc[4][2];
+    float scale;           // FP16 storage: stored value = population / scale
+    int* flag;             // non-finite flag (device)
+};
+
+// Population storage conversion.
+template <class S, class R>
+__device__ __forceinline__ R load_pop(const S* p, float) { return R(*p); }
+template <>
+__device__ __forceinline__ float load_pop<__half, float>(const __half* p, float scale) {
+    return __half2float(*p) * scale;
+}
+template <class S, class R>
+__device__ __forceinline__ void store_pop(S* p, R v, float) { *p = S(v); }
+template <>
+__device__ __forceinline__ void store_pop<__half, float>(__half* p, float v, float scale) {
+    *p = __float2half_rn(v / scale);
+}
+
+// Plane k of the stored state: k = 0..7 hold f_1..f_8, k = 8..16 hold h_0..h_8.
+constexpr int NPLANES = 17;
+
+template <class R>
+struct Pops {
+    R f[9];  // f[0] unused
+    R h[9];
+};
+
+template <class R>
+struct NodeState {
+    R th;               // T - T0
+    R ux, uy, Fx, Fy;   // velocity, total force
+    R p;
+    R Sxx, Sxy, Syy;    // shear rate
+    R gx, gy;           // grad T
+};
+
+// Role of node (x, y): interior, or a wall node with its NEES neighbours.
+struct WallInfo {
+    int wall;       // 0 interior
+    int xs, ys;     // node whose post-streaming state is used (x itself, or x_f)
+    int xff, yff;   // x_ff for the Neumann extrapolation
+    int tside;      // side whose Dirichlet T applies, -1: adiabatic
+    int uside;      // side whose wall velocity applies
+    int fixgx, fixgy;
+};
+
+template <class R>
+__device__ __forceinline__ WallInfo classify(const KConst<R>& k, int x, int y) {
+    WallInfo w;
+    const bool onW = x == 0 && k.bc[SW] != BC_PERIODIC;
+    const bool onE = x == k.nx - 1 && k.bc[SE] != BC_PERIODIC;
+    const bool onS = y == 0 && k.bc[SS] != BC_PERIODIC;
+    const bool onN = y == k.ny - 1 && k.bc[SN] != BC_PERIODIC;
+    w.wall = onW || onE || onS || onN;
+    const int dx = onW ? 1 : (onE ? -1 : 0);
+    const int dy = onS ? 1 : (onN ? -1 : 0);
+    w.xs = x + dx;
+    w.ys = y + dy;
+    w.xff = x + 2 * dx;
+    w.yff = y + 2 * dy;
+    const int xsd = onW ? SW : (onE ? SE : -1);
+    const int ysd = onS ? SS : (onN ? SN : -1);
+    w.tside = -1;
+    if (xsd >= 0 && k.bc[xsd] == BC_DIRICHLET) w.tside = xsd;
+    else if (ysd >= 0 && k.bc[ysd] == BC_DIRICHLET) w.tside = ysd;
+    w.uside = xsd >= 0 ? xsd : (ysd >= 0 ? ysd : 0);
+    w.fixgx = xsd >= 0;
+    w.fixgy = ysd >= 0;
+    return w;
+}
+
+// Post-streaming populations of node (x, y): f_i and g_i pulled from x - c_i.
+template <class R, class S>
+__device__ __forceinline__ void pull(const KConst<R>& k, const S* __restrict__ src, int x, int y,
+                                     Pops<R>& P) {
+    const int xm = x == 0 ? k.nx - 1 : x - 1;
+    const int xp = x == k.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? k.ny - 1 : y - 1;
+    const int yp = y == k.ny - 1 ? 0 : y + 1;
+    const long long r0 = (long long)y * k.pitch, rm = (long long)ym * k.pitch,
+                    rp = (long long)yp * k.pitch;
+    // source of direction i is x - c_i
+    const long long at[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x,
+                             rm + xm, rm + xp, rp + xp, rp + xm};
+    const float sc = k.scale;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) P.f[i] = load_pop<S, R>(src + (long long)(i - 1) * k.plane + at[i], sc);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) P.h[i] = load_pop<S, R>(src + (long long)(8 + i) * k.plane + at[i], sc);
+    P.f[0] = R(0);
+}
+
+// Sum of the thermal deviations pulled into (x, y), accumulated in Acc (for T alone).
+template <class Acc, class R, class S>
+__device__ __forceinline__ Acc pull_hsum(const KConst<R>& k, const S* __restrict__ src, int x, int y) {
+    const int xm = x == 0 ? k.nx - 1 : x - 1;
+    const int xp = x == k.nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? k.ny - 1 : y - 1;
+    const int yp = y == k.ny - 1 ? 0 : y + 1;
+    const long long r0 = (long long)y * k.pitch, rm = (long long)ym * k.pitch,
+                    rp = (long long)yp * k.pitch;
+    const long long at[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x,
+                             rm + xm, rm + xp, rp + xp, rp + xm};
+    Acc s = Acc(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) s += Acc(load_pop<S, R>(src + (long long)(8 + i) * k.plane + at[i], k.scale));
+    return s;
+}
+
+// Moments of one node from its post-streaming populations.
+template <class R>
+__device__ __forceinline__ NodeState<R> node_moments(const KConst<R>& k, const Pops<R>& P) {
+    NodeState<R> s;
+    const R* f = P.f;
+    const R* h = P.h;
+    // sigma T = sum g + Q/2, with sum g = sum h + sigma T0
+    R sh = h[0] + h[1] + h[2] + h[3] + h[4] + h[5] + h[6] + h[7] + h[8];
+    s.th = (sh + R(0.5) * k.Q) * k.inv_sigma;
+    const R T = k.T0 + s.th;
+    // flow moments
+    const R sf = f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    const R mx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const R my = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
+    const R d58 = f[5] + f[6] + f[7] + f[8];
+    const R Pxx = f[1] + f[3] + d58;
+    const R Pyy = f[2] + f[4] + d58;
+    const R Pxy = (f[5] + f[7]) - (f[6] + f[8]);
+    // buoyancy, temporary velocity, quadratic solve
+    const R Gx = k.ax;
+    const R Gy = k.gbeta * s.th + k.ay;
+    const R vx = mx / k.rho0 + R(0.5) * k.eps * Gx;
+    const R vy = my / k.rho0 + R(0.5) * k.eps * Gy;
+    const R vmag = sqrt(vx * vx + vy * vy);
+    const R den = k.c0 + sqrt(k.c0sq + k.c1 * vmag);
+    s.ux = vx / den;
+    s.uy = vy / den;
+    const R uu = s.ux * s.ux + s.uy * s.uy;
+    const R umag = sqrt(uu);
+    const R drag = k.e_nuK + k.e_FK * umag;
+    s.Fx = -drag * s.ux + k.eps * Gx;
+    s.Fy = -drag * s.uy + k.eps * Gy;
+    const R uF = s.ux * s.Fx + s.uy * s.Fy;
+    // p = c_s^2/(eps (1-w0)) [sum_{i!=0} f + tau_f F_0 + rho0 s_0],
+    // F_0 = -3 w0 rho0 kf u.F/eps, s_0 = -1.5 w0 |u|^2/eps, w0 = 4/9
+    const R F0 = -(R(4) / R(3)) * k.rho0 * k.kf * uF * k.inv_eps;
+    const R s0 = -(R(2) / R(3)) * uu * k.inv_eps;
+    s.p = k.p_pref * (sf + k.tau_f * F0 + k.rho0 * s0);
+    // S = [Pi - eps p I - rho0 u u/eps + (rho0/2)(uF + Fu)/eps] / (c_s^2 rho0 (A - tau_f))
+    const R re = k.rho0 * k.inv_eps;
+    const R ep = k.eps * s.p;
+    s.Sxx = (Pxx - ep - re * s.ux * s.ux + re * s.ux * s.Fx) * k.invD;
+    s.Syy = (Pyy - ep - re * s.uy * s.uy + re * s.uy * s.Fy) * k.invD;
+    s.Sxy = (Pxy - re * s.ux * s.uy + R(0.5) * re * (s.ux * s.Fy + s.Fx * s.uy)) * k.invD;
+    // N = sum c (g - g^{e(0)}) + (T F + u Q/sigma)/2 with sum c g^{e(0)} = T u
+    const R nx_ = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+    const R ny_ = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
+    const R qs = R(0.5) * k.Q * k.inv_sigma;
+    const R Nx = nx_ - T * s.ux + R(0.5) * T * s.Fx + qs * s.ux;
+    const R Ny = ny_ - T * s.uy + R(0.5) * T * s.Fy + qs * s.uy;
+    // M = a I - b u u^T, a = -eps p/(2 rho0) + c_s^2 sigma (B - tau_T),
+    // b = (1/eps - 1/sigma)/2; M^{-1} N = (N + b u (u.N)/(a - b|u|^2)) / a
+    const R a = -R(0.5) * ep / k.rho0 + k.a_const;
+    const R uN = s.ux * Nx + s.uy * Ny;
+    const R t = k.bcoef * uN / (a - k.bcoef * uu);
+    const R ia = R(1) / a;
+    s.gx = (Nx + t * s.ux) * ia;
+    s.gy = (Ny + t * s.uy) * ia;
+    return s;
+}
+
+// Equilibria and source terms of one state, direction by direction.
+template <class R>
+struct EqTerms {
+    R fe[9];   // f^eq_i, i = 1..8 (index 0 unused)
+    R Fi[9];   // forcing term F_i, i = 1..8
+    R he[9];   // g^eq_i - w_i sigma T0
+    R PQ[9];   // P_i + Q_i
+};
+
+template <class R>
+__device__ __forceinline__ void eq_terms(const KConst<R>& k, const NodeState<R>& s, EqTerms<R>& e) {
+    const R T = k.T0 + s.th;
+    const R uu = s.ux * s.ux + s.uy * s.uy;
+    const R ie = k.inv_eps;
+    const R flow_c = R(3) * k.eps * s.p - R(1.5) * k.rho0 * uu * ie - R(0.5) * k.rho0 * k.A * (s.Sxx + s.Syy);
+    const R uF = s.ux * s.Fx + s.uy * s.Fy;
+    const R force_c = -R(3) * uF * ie;
+    const R pT = R(3) * T * k.eps * s.p / k.rho0;   // 3 T eps p / rho0
+    const R ug = s.ux * s.gx + s.uy * s.gy;
+    const R Wx = T * s.Fx + k.eps * s.p * s.gx / k.rho0;
+    const R Wy = T * s.Fy + k.eps * s.p * s.gy / k.rho0;
+    const R therm_c = k.sigma * s.th - R(1.5) * T * uu * ie;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const R cx = R(cx_of(i)), cy = R(cy_of(i));
+        const R w = w_of<R>(i);
+        const R cu = cx * s.ux + cy * s.uy;
+        const R cF = cx * s.Fx + cy * s.Fy;
+        if (i > 0) {
+            const R ScS = cx * cx * s.Sxx + R(2) * cx * cy * s.Sxy + cy * cy * s.Syy;
+            e.fe[i] = w * (flow_c + k.rho0 * (R(3) * cu + R(4.5) * cu * cu * ie) + R(1.5) * k.rho0 * k.A * ScS);
+            e.Fi[i] = w * k.rho0 * k.kf * (R(3) * cF + R(9) * cu * cF * ie + force_c);
+        } else {
+            e.fe[0] = R(0);
+            e.Fi[0] = R(0);
+        }
+        const R cg = cx * s.gx + cy * s.gy;
+        // varpi_0 = -5/9 = -(1 - w0); varpi_i = w_i otherwise
+        const R pv = (i == 0) ? -(R(5) / R(9)) * pT : w * pT;
+        e.he[i] = w * (therm_c + T * (R(3) * cu + R(4.5) * cu * cu * ie) + k.sigma * k.B * cg) + pv;
+        const R cW = cx * Wx + cy * Wy;
+        e.PQ[i] = w * k.kT * (R(3) * cW + R(6) * k.bcoef * cu * ug + (R(1) + R(3) * cu * k.inv_sigma) * k.Q);
+    }
+}
+
+// Boundary state of a wall node (Sec. 3.4): u_b, T_b, p(x_f), S(x_f),
+// grad T_b, and F at (u_b, T_b).  thff is T(x_ff) - T0 (adiabatic walls only).
+template <class R>
+__device__ __forceinline__ NodeState<R> wall_state(const KConst<R>& k, const WallInfo& w,
+                                                   const NodeState<R>& sf, R thff) {
+    NodeState<R> b = sf;
+    b.ux = k.u_bc[w.uside][0];
+    b.uy = k.u_bc[w.uside][1];
+    if (w.tside >= 0) {
+        b.th = k.T_bc[w.tside] - k.T0;
+    } else {
+        // Eq. (TNEESApGra) with zero normal gradient
+        if (w.fixgx) b.gx = R(0);
+        if (w.fixgy) b.gy = R(0);
+        b.th = (R(4) * sf.th - thff) * (R(1) / R(3));
+    }
+    const R umag = sqrt(b.ux * b.ux + b.uy * b.uy);
+    const R drag = k.e_nuK + k.e_FK * umag;
+    b.Fx = -drag * b.ux + k.eps * k.ax;
+    b.Fy = -drag * b.uy + k.eps * (k.gbeta * b.th + k.ay);
+    return b;
+}
+
+}  // namespace lbm

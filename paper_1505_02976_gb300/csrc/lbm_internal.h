@@ -1,0 +1,51 @@
+// lbm_internal.h -- launch wrappers shared by the host API and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Double-precision constants for the diagnostics (temperatures for the
+// Nusselt number are taken in FP64 from the stored populations).
+struct DiagConst {
+    double T0, inv_sigma, Q, L, dT;
+    double T_bc[4];
+};
+
+template <class R, class S>
+cudaError_t launch_step(const KConst<R>& k, const S* src, S* dst, cudaStream_t st);
+
+template <class R, class S>
+cudaError_t launch_init(const KConst<R>& k, S* dst, const double* T, const double* ux,
+                        const double* uy, double T_init, cudaStream_t st);
+
+template <class R, class S>
+cudaError_t launch_moments(const KConst<R>& k, const S* src, double* p, double* ux, double* uy,
+                           double* T, cudaStream_t st);
+
+template <class R, class S>
+cudaError_t launch_get_state(const KConst<R>& k, const S* src, double* f, double* g,
+                             double sT0, cudaStream_t st);
+
+template <class R, class S>
+cudaError_t launch_set_state(const KConst<R>& k, S* dst, const double* f, const double* g,
+                             double sT0, cudaStream_t st);
+
+// Local Nusselt numbers along one side into nu_local, then their trapezoid
+// mean into out[0] (deterministic single-block reduction).
+template <class R, class S>
+cudaError_t launch_nusselt(const KConst<R>& k, const DiagConst& d, const S* src, int side,
+                           double* nu_local, double* out, cudaStream_t st);
+
+// Residual sums (|du|, |u|, |dT|, |T|) into out[0..3] against snap (3 planes
+// of nx*ny doubles: ux, uy, T), which is overwritten with the current fields.
+// partial must hold 4 doubles per block of the launch (see residual_blocks).
+template <class R, class S>
+cudaError_t launch_residual(const KConst<R>& k, const S* src, double* snap, double* partial,
+                            double* out, cudaStream_t st);
+
+long long residual_blocks(int nx, int ny);
+
+}  // namespace lbm

@@ -1,0 +1,334 @@
+// lbm_kernels.cu -- the fused step kernel and the small auxiliary kernels.
+//
+// k_step: one thread per node, pull streaming from the ping buffer, all the
+// per-node arithmetic of the step in registers, NEES wall rebuild fused in
+// (the wall thread pulls its x_f neighbour's populations instead of its own,
+// so every thread runs the same moment code; only the collision differs), and
+// one write of the 17 post-collision planes to the pong buffer.
+#include <math.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+constexpr int kStepBlock = 128;
+
+template <class R, class S>
+__device__ __forceinline__ void store_node(const KConst<R>& k, S* __restrict__ dst, long long at,
+                                           const R* fo, const R* ho) {
+#pragma unroll
+    for (int i = 1; i < 9; ++i) store_pop<S, R>(dst + (long long)(i - 1) * k.plane + at, fo[i], k.scale);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) store_pop<S, R>(dst + (long long)(8 + i) * k.plane + at, ho[i], k.scale);
+}
+
+// Boundary state of a wall node, or the node's own state.
+template <class R, class S>
+__device__ __forceinline__ NodeState<R> target_state(const KConst<R>& k, const S* __restrict__ src,
+                                                     const WallInfo& w, const NodeState<R>& s) {
+    if (!w.wall) return s;
+    R thff = R(0);
+    if (w.tside < 0) thff = (pull_hsum<R, R, S>(k, src, w.xff, w.yff) + R(0.5) * k.Q) * k.inv_sigma;
+    return wall_state(k, w, s, thff);
+}
+
+template <class R, class S>
+__global__ void __launch_bounds__(kStepBlock)
+k_step(const __grid_constant__ KConst<R> k, const S* __restrict__ src, S* __restrict__ dst) {
+    const int x = blockIdx.x * kStepBlock + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= k.nx) return;
+    const WallInfo w = classify(k, x, y);
+    Pops<R> P;
+    pull(k, src, w.wall ? w.xs : x, w.wall ? w.ys : y, P);
+    const NodeState<R> s = node_moments(k, P);
+    if (!(isfinite(s.th) && isfinite(s.ux) && isfinite(s.uy))) atomicOr(k.flag, 1);
+    EqTerms<R> e;
+    eq_terms(k, s, e);
+    R fo[9], ho[9];
+    if (!w.wall) {
+        // BGK collision, Eqs. (LBEeq), (TEqColli)
+#pragma unroll
+        for (int i = 1; i < 9; ++i) fo[i] = e.fe[i] + k.omf * (P.f[i] - e.fe[i]) + e.Fi[i];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ho[i] = e.he[i] + k.omT * (P.h[i] - e.he[i]) + e.PQ[i];
+    } else {
+        // NEES rebuild (Eqs. NEESVel, TNEESAp) followed by the collision with
+        // the boundary equilibrium: f* = f^eq(x_b) + (1 - 1/tau)[f(x_f) - f^eq(x_f)] + F_i(x_b)
+        R nf[9], nh[9];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) nf[i] = P.f[i] - e.fe[i];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) nh[i] = P.h[i] - e.he[i];
+        const NodeState<R> b = target_state(k, src, w, s);
+        EqTerms<R> eb;
+        eq_terms(k, b, eb);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) fo[i] = eb.fe[i] + k.omf * nf[i] + eb.Fi[i];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ho[i] = eb.he[i] + k.omT * nh[i] + eb.PQ[i];
+    }
+    store_node(k, dst, (long long)y * k.pitch + x, fo, ho);
+}
+
+template <class R, class S>
+__global__ void k_init(const __grid_constant__ KConst<R> k, S* __restrict__ dst,
+                       const double* __restrict__ T, const double* __restrict__ ux,
+                       const double* __restrict__ uy, double T_init) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= k.nx) return;
+    const long long c = (long long)y * k.nx + x;
+    NodeState<R> s;
+    s.th = R((T ? T[c] : T_init) - double(k.T0));
+    s.ux = ux ? R(ux[c]) : R(0);
+    s.uy = uy ? R(uy[c]) : R(0);
+    s.p = R(0);
+    s.Fx = s.Fy = R(0);
+    s.Sxx = s.Sxy = s.Syy = R(0);
+    s.gx = s.gy = R(0);
+    EqTerms<R> e;
+    eq_terms(k, s, e);
+    store_node(k, dst, (long long)y * k.pitch + x, e.fe, e.he);
+}
+
+template <class R, class S>
+__global__ void k_moments(const __grid_constant__ KConst<R> k, const S* __restrict__ src,
+                          double* __restrict__ p, double* __restrict__ ux, double* __restrict__ uy,
+                          double* __restrict__ T) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= k.nx) return;
+    const WallInfo w = classify(k, x, y);
+    Pops<R> P;
+    pull(k, src, w.wall ? w.xs : x, w.wall ? w.ys : y, P);
+    const NodeState<R> s = target_state(k, src, w, node_moments(k, P));
+    const long long c = (long long)y * k.nx + x;
+    p[c] = double(s.p);
+    ux[c] = double(s.ux);
+    uy[c] = double(s.uy);
+    T[c] = double(k.T0) + double(s.th);
+}
+
+template <class R, class S>
+__global__ void k_get_state(const __grid_constant__ KConst<R> k, const S* __restrict__ src,
+                            double* __restrict__ f, double* __restrict__ g, double sT0) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= k.nx) return;
+    const long long at = (long long)y * k.pitch + x;
+    const long long c = (long long)y * k.nx + x;
+    const long long N = (long long)k.nx * k.ny;
+    f[c] = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) f[i * N + c] = double(load_pop<S, R>(src + (long long)(i - 1) * k.plane + at, k.scale));
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        g[i * N + c] = double(load_pop<S, R>(src + (long long)(8 + i) * k.plane + at, k.scale)) + w_of<double>(i) * sT0;
+}
+
+template <class R, class S>
+__global__ void k_set_state(const __grid_constant__ KConst<R> k, S* __restrict__ dst,
+                            const double* __restrict__ f, const double* __restrict__ g, double sT0) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= k.nx) return;
+    const long long at = (long long)y * k.pitch + x;
+    const long long c = (long long)y * k.nx + x;
+    const long long N = (long long)k.nx * k.ny;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) store_pop<S, R>(dst + (long long)(i - 1) * k.plane + at, R(f[i * N + c]), k.scale);
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        store_pop<S, R>(dst + (long long)(8 + i) * k.plane + at, R(g[i * N + c] - w_of<double>(i) * sT0), k.scale);
+}
+
+// T of node (x, y) in FP64 from the stored populations, with the wall rules
+// of Sec. 3.4 (Dirichlet value, or Eq. TNEESApGra on adiabatic walls).
+template <class R, class S>
+__device__ double node_T(const KConst<R>& k, const DiagConst& d, const S* __restrict__ src, int x, int y) {
+    const WallInfo w = classify(k, x, y);
+    if (!w.wall) return d.T0 + (pull_hsum<double, R, S>(k, src, x, y) + 0.5 * d.Q) * d.inv_sigma;
+    if (w.tside >= 0) return d.T_bc[w.tside];
+    const double tf = (pull_hsum<double, R, S>(k, src, w.xs, w.ys) + 0.5 * d.Q) * d.inv_sigma;
+    const double tff = (pull_hsum<double, R, S>(k, src, w.xff, w.yff) + 0.5 * d.Q) * d.inv_sigma;
+    return d.T0 + (4.0 * tf - tff) / 3.0;
+}
+
+template <class R, class S>
+__global__ void k_nusselt_local(const __grid_constant__ KConst<R> k, const DiagConst d,
+                                const S* __restrict__ src, int side, double* __restrict__ nu) {
+    const int n = side <= SE ? k.ny : k.nx;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double t[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        int x, y;
+        if (side == SW) { x = m; y = j; }
+        else if (side == SE) { x = k.nx - 1 - m; y = j; }
+        else if (side == SS) { x = j; y = m; }
+        else { x = j; y = k.ny - 1 - m; }
+        t[m] = node_T(k, d, src, x, y);
+    }
+    // derivative from the wall inward, then along +x (W, E) or +y (S, N)
+    const double d_in = (-3.0 * t[0] + 4.0 * t[1] - t[2]) * 0.5;
+    const double d_axis = (side == SW || side == SS) ? d_in : -d_in;
+    nu[j] = -d.L * d_axis / d.dT;
+}
+
+constexpr int kReduceBlock = 256;
+
+// Fixed-order block sum of one value per thread (deterministic).
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    return s;  // valid in thread 0
+}
+
+__global__ void k_nusselt_mean(const double* __restrict__ nu, int n, double* __restrict__ out) {
+    __shared__ double sh[kReduceBlock / 32];
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < n; j += kReduceBlock) acc += ((j == 0 || j == n - 1) ? 0.5 : 1.0) * nu[j];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[0] = s / double(n - 1);
+}
+
+constexpr int kResBlock = 128;
+
+template <class R, class S>
+__global__ void __launch_bounds__(kResBlock)
+k_residual(const __grid_constant__ KConst<R> k, const S* __restrict__ src, double* __restrict__ snap,
+           double* __restrict__ partial) {
+    __shared__ double sh[kResBlock / 32];
+    const int x = blockIdx.x * kResBlock + threadIdx.x;
+    const int y = blockIdx.y;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (x < k.nx) {
+        const WallInfo w = classify(k, x, y);
+        Pops<R> P;
+        pull(k, src, w.wall ? w.xs : x, w.wall ? w.ys : y, P);
+        const NodeState<R> s = target_state(k, src, w, node_moments(k, P));
+        const long long N = (long long)k.nx * k.ny;
+        const long long c = (long long)y * k.nx + x;
+        const double ux = double(s.ux), uy = double(s.uy), T = double(k.T0) + double(s.th);
+        const double dx = ux - snap[c], dy = uy - snap[N + c], dT = T - snap[2 * N + c];
+        v[0] = sqrt(dx * dx + dy * dy);
+        v[1] = sqrt(ux * ux + uy * uy);
+        v[2] = fabs(dT);
+        v[3] = fabs(T);
+        snap[c] = ux;
+        snap[N + c] = uy;
+        snap[2 * N + c] = T;
+    }
+    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const double s = block_sum(v[m], sh);
+        if (threadIdx.x == 0) partial[4 * b + m] = s;
+    }
+}
+
+__global__ void k_reduce4(const double* __restrict__ partial, long long nb, double* __restrict__ out) {
+    __shared__ double sh[kReduceBlock / 32];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long b = threadIdx.x; b < nb; b += kReduceBlock)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) a[m] += partial[4 * b + m];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const double s = block_sum(a[m], sh);
+        if (threadIdx.x == 0) out[m] = s;
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+static dim3 row_grid(int nx, int ny, int bx) { return dim3((unsigned)((nx + bx - 1) / bx), (unsigned)ny); }
+
+long long residual_blocks(int nx, int ny) {
+    return (long long)((nx + kResBlock - 1) / kResBlock) * ny;
+}
+
+template <class R, class S>
+cudaError_t launch_step(const KConst<R>& k, const S* src, S* dst, cudaStream_t st) {
+    k_step<R, S><<<row_grid(k.nx, k.ny, kStepBlock), kStepBlock, 0, st>>>(k, src, dst);
+    return cudaGetLastError();
+}
+
+template <class R, class S>
+cudaError_t launch_init(const KConst<R>& k, S* dst, const double* T, const double* ux,
+                        const double* uy, double T_init, cudaStream_t st) {
+    k_init<R, S><<<row_grid(k.nx, k.ny, 128), 128, 0, st>>>(k, dst, T, ux, uy, T_init);
+    return cudaGetLastError();
+}
+
+template <class R, class S>
+cudaError_t launch_moments(const KConst<R>& k, const S* src, double* p, double* ux, double* uy,
+                           double* T, cudaStream_t st) {
+    k_moments<R, S><<<row_grid(k.nx, k.ny, 128), 128, 0, st>>>(k, src, p, ux, uy, T);
+    return cudaGetLastError();
+}
+
+template <class R, class S>
+cudaError_t launch_get_state(const KConst<R>& k, const S* src, double* f, double* g, double sT0,
+                             cudaStream_t st) {
+    k_get_state<R, S><<<row_grid(k.nx, k.ny, 128), 128, 0, st>>>(k, src, f, g, sT0);
+    return cudaGetLastError();
+}
+
+template <class R, class S>
+cudaError_t launch_set_state(const KConst<R>& k, S* dst, const double* f, const double* g,
+                             double sT0, cudaStream_t st) {
+    k_set_state<R, S><<<row_grid(k.nx, k.ny, 128), 128, 0, st>>>(k, dst, f, g, sT0);
+    return cudaGetLastError();
+}
+
+template <class R, class S>
+cudaError_t launch_nusselt(const KConst<R>& k, const DiagConst& d, const S* src, int side,
+                           double* nu_local, double* out, cudaStream_t st) {
+    const int n = side <= SE ? k.ny : k.nx;
+    k_nusselt_local<R, S><<<(n + 127) / 128, 128, 0, st>>>(k, d, src, side, nu_local);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_nusselt_mean<<<1, kReduceBlock, 0, st>>>(nu_local, n, out);
+    return cudaGetLastError();
+}
+
+template <class R, class S>
+cudaError_t launch_residual(const KConst<R>& k, const S* src, double* snap, double* partial,
+                            double* out, cudaStream_t st) {
+    k_residual<R, S><<<row_grid(k.nx, k.ny, kResBlock), kResBlock, 0, st>>>(k, src, snap, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce4<<<1, kReduceBlock, 0, st>>>(partial, residual_blocks(k.nx, k.ny), out);
+    return cudaGetLastError();
+}
+
+#define LBM_INSTANTIATE(R, S)                                                                        \
+    template cudaError_t launch_step<R, S>(const KConst<R>&, const S*, S*, cudaStream_t);           \
+    template cudaError_t launch_init<R, S>(const KConst<R>&, S*, const double*, const double*,      \
+                                           const double*, double, cudaStream_t);                    \
+    template cudaError_t launch_moments<R, S>(const KConst<R>&, const S*, double*, double*, double*, \
+                                              double*, cudaStream_t);                               \
+    template cudaError_t launch_get_state<R, S>(const KConst<R>&, const S*, double*, double*,       \
+                                                double, cudaStream_t);                              \
+    template cudaError_t launch_set_state<R, S>(const KConst<R>&, S*, const double*, const double*, \
+                                                double, cudaStream_t);                              \
+    template cudaError_t launch_nusselt<R, S>(const KConst<R>&, const DiagConst&, const S*, int,    \
+                                              double*, double*, cudaStream_t);                      \
+    template cudaError_t launch_residual<R, S>(const KConst<R>&, const S*, double*, double*,        \
+                                               double*, cudaStream_t);
+
+LBM_INSTANTIATE(double, double)
+LBM_INSTANTIATE(float, float)
+LBM_INSTANTIATE(float, __half)
+
+}  // namespace lbm

@@ -1,0 +1,252 @@
+"""Python binding of the C ABI in ``include/lbm.h`` (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+``liblbm_gb300.so``.  PyTorch supplies the device workspace and the stream.
+The functions keep the C names (``lbm_create``, ``lbm_step``, ...); the
+``Lattice`` class wraps one handle.  There is no CPU fallback: without the
+built library or a CUDA device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK = 0
+STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NONFINITE",
+          -4: "LBM_ERR_TIMEOUT", -5: "LBM_ERR_PARAM_RANGE", -6: "LBM_ERR_OOM"}
+PRECISION = {"f64": 0, "f32": 1, "f16": 2}
+BC = {"periodic": 0, "dirichlet": 1, "adiabatic": 2}
+SIDE = {"W": 0, "E": 1, "S": 2, "N": 3}
+
+EXPORTED = ("lbm_params_default", "lbm_derived", "lbm_workspace_size", "lbm_create", "lbm_destroy",
+            "lbm_last_error", "lbm_set_fields", "lbm_step", "lbm_sync", "lbm_moments", "lbm_nusselt",
+            "lbm_residual", "lbm_get_state", "lbm_set_state", "lbm_steps_done",
+            "lbm_kernel_launches")
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class lbm_params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("bc", C.c_int32 * 4),
+        ("forchheimer", C.c_int32), ("da_infinite", C.c_int32),
+        ("precision", C.c_int32), ("reserved", C.c_int32),
+        ("Ra", C.c_double), ("Pr", C.c_double), ("Da", C.c_double), ("J", C.c_double),
+        ("eps", C.c_double), ("sigma", C.c_double), ("Ma", C.c_double),
+        ("tau_f", C.c_double), ("tau_T", C.c_double),
+        ("Th", C.c_double), ("Tc", C.c_double), ("T_init", C.c_double), ("rho0", C.c_double),
+        ("Q", C.c_double), ("ax", C.c_double), ("ay", C.c_double),
+        ("L", C.c_double), ("nu", C.c_double), ("alpha_e", C.c_double), ("gbeta", C.c_double),
+        ("A", C.c_double), ("B", C.c_double), ("K", C.c_double),
+        ("T_bc", C.c_double * 4), ("u_bc", (C.c_double * 2) * 4),
+    ]
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load the in-tree library (building it first when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise LbmError(-2, f"CUDA library not built: {path}")
+        _build.build()
+    L = C.CDLL(path)
+    P = C.POINTER(lbm_params)
+    H = C.c_void_p
+    dp = C.POINTER(C.c_double)
+    L.lbm_params_default.argtypes = [P]
+    L.lbm_derived.argtypes = [P, dp]
+    L.lbm_workspace_size.argtypes = [P, C.POINTER(C.c_size_t)]
+    L.lbm_create.argtypes = [P, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(H)]
+    L.lbm_destroy.argtypes = [H]
+    L.lbm_destroy.restype = None
+    L.lbm_last_error.argtypes = [H]
+    L.lbm_last_error.restype = C.c_char_p
+    L.lbm_set_fields.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    L.lbm_step.argtypes = [H, C.c_int64]
+    L.lbm_sync.argtypes = [H]
+    L.lbm_moments.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+    L.lbm_nusselt.argtypes = [H, C.c_int, dp, C.c_void_p]
+    L.lbm_residual.argtypes = [H, dp, dp]
+    L.lbm_get_state.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int]
+    L.lbm_set_state.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int]
+    L.lbm_steps_done.argtypes = [H]
+    L.lbm_steps_done.restype = C.c_int64
+    L.lbm_kernel_launches.argtypes = [H]
+    L.lbm_kernel_launches.restype = C.c_int64
+    for name in EXPORTED:
+        if name not in ("lbm_destroy", "lbm_last_error", "lbm_steps_done", "lbm_kernel_launches"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _nan(v):
+    return float("nan") if v is None else float(v)
+
+
+def params_from_problem(p: dict, precision: str = "f32") -> lbm_params:
+    """Marshal a problem dict (``workloads.problem``) into ``lbm_params``."""
+    s = lbm_params()
+    s.nx, s.ny = int(p["nx"]), int(p["ny"])
+    for k, b in enumerate(p["bc"]):
+        s.bc[k] = BC[b]
+    s.forchheimer = int(p["forchheimer"])
+    s.da_infinite = int(p["da_infinite"])
+    s.precision = PRECISION[precision]
+    s.reserved = 0
+    for name in ("Ra", "Pr", "Da", "J", "eps", "sigma", "Ma", "tau_f", "tau_T", "Th", "Tc",
+                 "T_init", "rho0", "Q", "ax", "ay"):
+        setattr(s, name, float(p[name]))
+    for name in ("L", "nu", "alpha_e", "gbeta", "A", "B", "K"):
+        setattr(s, name, _nan(p[name]))
+    for k in range(4):
+        s.T_bc[k] = float(p["T_bc"][k])
+        s.u_bc[k][0] = float(p["u_bc"][k][0])
+        s.u_bc[k][1] = float(p["u_bc"][k][1])
+    return s
+
+
+def _check(status: int, handle=None):
+    if status != LBM_OK:
+        msg = load().lbm_last_error(handle)
+        raise LbmError(status, msg.decode() if msg else "")
+
+
+DERIVED_KEYS = ("L", "T0", "dT", "U", "gbeta", "nu", "nu_e", "alpha_e", "A", "B", "K", "Feps")
+
+
+def lbm_derived(p: dict) -> dict:
+    out = (C.c_double * 12)()
+    _check(load().lbm_derived(C.byref(params_from_problem(p)), out))
+    return dict(zip(DERIVED_KEYS, list(out)))
+
+
+def lbm_workspace_size(p: dict, precision: str = "f32") -> int:
+    n = C.c_size_t()
+    _check(load().lbm_workspace_size(C.byref(params_from_problem(p, precision)), C.byref(n)))
+    return int(n.value)
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor, or host pointer of a numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Lattice:
+    """One lattice on the current CUDA device, advanced by the fused kernel.
+
+    ``Lattice(problem, precision)`` creates the handle with a torch-allocated
+    workspace on ``device`` and the current torch stream of that device."""
+
+    def __init__(self, problem: dict, precision: str = "f32", device: int = 0, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise LbmError(-2, "no CUDA device: the library has no CPU path")
+        self.lib = load()
+        self.problem = dict(problem)
+        self.precision = precision
+        self.nx, self.ny = int(problem["nx"]), int(problem["ny"])
+        self.params = params_from_problem(problem, precision)
+        self.device = torch.device("cuda", device)
+        nbytes = lbm_workspace_size(problem, precision)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        _check(self.lib.lbm_create(C.byref(self.params), C.c_void_p(self.stream.cuda_stream),
+                                   _ptr(self.workspace), nbytes, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- state
+    def set_fields(self, T=None, ux=None, uy=None):
+        on_dev = any(hasattr(a, "data_ptr") for a in (T, ux, uy) if a is not None)
+        conv = (lambda a: a) if on_dev else (lambda a: None if a is None else np.ascontiguousarray(a, np.float64))
+        T, ux, uy = conv(T), conv(ux), conv(uy)
+        _check(self.lib.lbm_set_fields(self.h, _ptr(T), _ptr(ux), _ptr(uy), None, int(on_dev)), self.h)
+
+    def step(self, n: int = 1):
+        _check(self.lib.lbm_step(self.h, int(n)), self.h)
+
+    def sync(self):
+        _check(self.lib.lbm_sync(self.h), self.h)
+
+    def moments(self) -> dict:
+        shape = (self.ny, self.nx)
+        out = {k: np.empty(shape) for k in ("p", "ux", "uy", "T")}
+        _check(self.lib.lbm_moments(self.h, _ptr(out["p"]), _ptr(out["ux"]), _ptr(out["uy"]),
+                                    _ptr(out["T"]), 0), self.h)
+        return out
+
+    def moments_device(self, out: dict):
+        """Write the moment fields into float64 torch tensors (asynchronous)."""
+        _check(self.lib.lbm_moments(self.h, _ptr(out.get("p")), _ptr(out.get("ux")),
+                                    _ptr(out.get("uy")), _ptr(out.get("T")), 1), self.h)
+
+    def nusselt(self, side="W"):
+        k = SIDE[side] if isinstance(side, str) else int(side)
+        n = self.ny if k <= 1 else self.nx
+        loc = np.empty(n)
+        mean = C.c_double()
+        _check(self.lib.lbm_nusselt(self.h, k, C.byref(mean), _ptr(loc)), self.h)
+        return mean.value, loc
+
+    def residual(self):
+        ru, rT = C.c_double(), C.c_double()
+        _check(self.lib.lbm_residual(self.h, C.byref(ru), C.byref(rT)), self.h)
+        return ru.value, rT.value
+
+    def get_state(self):
+        shape = (9, self.ny, self.nx)
+        f = np.empty(shape)
+        g = np.empty(shape)
+        _check(self.lib.lbm_get_state(self.h, _ptr(f), _ptr(g), 0), self.h)
+        return f, g
+
+    def set_state(self, f, g):
+        f = np.ascontiguousarray(f, np.float64)
+        g = np.ascontiguousarray(g, np.float64)
+        _check(self.lib.lbm_set_state(self.h, _ptr(f), _ptr(g), 0), self.h)
+
+    @property
+    def steps(self) -> int:
+        return int(self.lib.lbm_steps_done(self.h))
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.lbm_kernel_launches(self.h))
+
+
+def mlups(nx: int, ny: int, steps: int, seconds: float) -> float:
+    """Million lattice updates per second, all nodes counted."""
+    return nx * ny * steps / seconds / 1e6 if seconds > 0 else math.nan

@@ -59,11 +59,13 @@ def problem(**kw) -> dict:
     return p
 
 
-def cavity(n: int, Ra: float, Da: float, eps: float, Pr: float = 1.0, **kw) -> dict:
-    """Square porous cavity of Sec. 4.2 (Table 2 family): n x n nodes,
-    wall nodes included, left wall hot (Th = 1), right wall cold (Tc = 0),
-    adiabatic top and bottom, no slip everywhere, u = 0 and T = 0.5 at t = 0."""
-    return problem(nx=n, ny=n, Ra=Ra, Da=Da, eps=eps, Pr=Pr, **kw)
+def cavity(n: int, Ra: float, Da: float, eps: float, Pr: float = 1.0, ny: int | None = None,
+           **kw) -> dict:
+    """Porous cavity of Sec. 4.2 (Table 2 family): n x n nodes (n x ny when
+    ny is given), wall nodes included, left wall hot (Th = 1), right wall cold
+    (Tc = 0), adiabatic top and bottom, no slip everywhere, u = 0 and T = 0.5
+    at t = 0."""
+    return problem(nx=n, ny=ny or n, Ra=Ra, Da=Da, eps=eps, Pr=Pr, **kw)
 
 
 def poiseuille(nx: int = 8, ny: int = 64, G: float = 1e-5, eps: float = 0.5,
