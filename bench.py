@@ -332,9 +332,14 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None,
+                    help="lattice size override (profiling captures only; changes the workload)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.n:
+        WORKLOAD["n"] = args.n
+        WORKLOAD["name"] = f"cavity{args.n}_{WORKLOAD['precision']}"
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
