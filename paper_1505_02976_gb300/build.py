@@ -18,7 +18,8 @@ LIB = os.path.join(OUT, "liblbm_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "--expt-relaxed-constexpr", "-I", INCLUDE] + ARCH
+              "--expt-relaxed-constexpr", "-ftz=true", "-prec-div=false", "-prec-sqrt=false",
+              "-I", INCLUDE] + ARCH
 _lock = threading.Lock()
 
 

@@ -18,6 +18,7 @@ namespace {
 
 constexpr double kCs2 = 1.0 / 3.0;
 constexpr double kW0 = 4.0 / 9.0;
+constexpr int NPLANES_HOST = lbm::NPLANES;
 
 struct Derived {
     double L, T0, dT, U, gbeta, nu, nu_e, alpha_e, A, B, K, Feps;
@@ -74,6 +75,10 @@ lbm_status check_shape(const lbm_params* p, std::string* why) {
     }
     if ((p->bc[0] != LBM_BC_PERIODIC && p->nx < 4) || (p->bc[2] != LBM_BC_PERIODIC && p->ny < 4)) {
         *why = "a walled direction needs at least 4 nodes";
+        return LBM_ERR_ARG;
+    }
+    if ((double)NPLANES_HOST * (double)((size_t)p->nx + 128) * (double)p->ny >= 2147483647.0) {
+        *why = "lattice too large for 32-bit plane offsets (17 nx ny < 2^31)";
         return LBM_ERR_ARG;
     }
     if (p->precision < LBM_F64 || p->precision > LBM_F16 || p->reserved != 0) {
@@ -164,6 +169,40 @@ lbm::KConst<R> make_kconst(const lbm_params* p, const Derived& d, const Layout& 
     }
     k.scale = p->precision == LBM_F16 ? ldexpf(1.0f, -10) : 1.0f;
     k.flag = flag;
+    k.plane32 = (int)L.plane_elems;
+    // interior fast path: h* = (1 - 1/tau) h + [h^eq / tau + source], split
+    // into parts even and odd in c_i (lbm_device.cuh, interior_update)
+    const double rho0 = p->rho0, ie = 1.0 / eps, itf = 1.0 / p->tau_f, itT = 1.0 / p->tau_T;
+    const double kf = 1.0 - 0.5 / p->tau_f, kT = 1.0 - 0.5 / p->tau_T;
+    const double bc = 0.5 * (1.0 / eps - 1.0 / p->sigma);
+    k.inv_rho0 = R(1.0 / rho0);
+    k.half_eps_ax = R(0.5 * eps * p->ax);
+    k.half_eps = R(0.5 * eps);
+    k.p_uF = R(kCs2 / (eps * (1.0 - kW0)) * (4.0 / 3.0) * rho0 * kf * p->tau_f * ie);
+    k.p_uu = R(kCs2 / (eps * (1.0 - kW0)) * (2.0 / 3.0) * rho0 * ie);
+    k.fA_ep = R(3.0 * itf);
+    k.fA_uu = R(1.5 * itf * rho0 * ie);
+    k.fA_tr = R(0.5 * itf * rho0 * d.A);
+    k.fA_uF = R(3.0 * rho0 * kf * ie);
+    k.f_cu2 = R(4.5 * itf * rho0 * ie);
+    k.f_ScS = R(1.5 * itf * rho0 * d.A);
+    k.f_cucF = R(9.0 * rho0 * kf * ie);
+    k.f_cu = R(3.0 * rho0 * itf);
+    k.f_cF = R(3.0 * rho0 * kf);
+    k.h_sig = R(itT * p->sigma);
+    k.h_uu = R(itT * 1.5 * ie);
+    k.h_pT = R(itT * 3.0 / rho0);
+    k.h_kQ = R(kT * p->Q);
+    k.h_cu2 = R(itT * 4.5 * ie);
+    k.h_u3 = R(3.0 * itT);
+    k.h_ug = R(6.0 * kT * bc);
+    k.h_uQ = R(3.0 * kT * p->Q / p->sigma);
+    k.h_g = R(itT * p->sigma * d.B);
+    k.h_W = R(3.0 * kT);
+    k.h0_sig = R(itT * kW0 * p->sigma);
+    k.h0_uu = R(itT * kW0 * 1.5 * ie);
+    k.h0_pT = R(itT * (5.0 / 3.0) / rho0);
+    k.h0_kQ = R(kW0 * kT * p->Q);
     return k;
 }
 

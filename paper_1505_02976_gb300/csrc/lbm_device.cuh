@@ -67,6 +67,12 @@ struct KConst {
     R u_bc[4][2];
     float scale;           // FP16 storage: stored value = population / scale
     int* flag;             // non-finite flag (device)
+    int plane32;           // plane stride as a 32-bit offset (17 planes < 2^31 elements)
+    // constants of the interior fast path (see interior_update)
+    R inv_rho0, half_eps_ax, half_eps, p_uF, p_uu;
+    R fA_ep, fA_uu, fA_tr, fA_uF, f_cu2, f_ScS, f_cucF, f_cu, f_cF;
+    R h_sig, h_uu, h_pT, h_kQ, h_cu2, h_u3, h_ug, h_uQ, h_g, h_W;
+    R h0_sig, h0_uu, h0_pT, h0_kQ;
 };
 
 // Population storage conversion.
@@ -301,6 +307,102 @@ __device__ __forceinline__ NodeState<R> wall_state(const KConst<R>& k, const Wal
     b.Fx = -drag * b.ux + k.eps * k.ax;
     b.Fy = -drag * b.uy + k.eps * (k.gbeta * b.th + k.ay);
     return b;
+}
+
+// Interior node of one step, fast path.  Same arithmetic as node_moments +
+// eq_terms + BGK collision, rearranged for the GPU:
+//  * the nine pull sources are 32-bit offsets from the node (periodic wrap by
+//    per-thread deltas), plane strides are uniform across the launch;
+//  * the collision is written as h_i* = (1 - 1/tau) h_i + [h_i^eq/tau + source_i]
+//    and the bracket is split into the parts that are even and odd under
+//    c_i -> -c_i, so each pair of opposite directions shares one evaluation.
+template <class R, class S>
+__device__ __forceinline__ void interior_update(const KConst<R>& k, const S* __restrict__ src,
+                                                S* __restrict__ dst, int x, int y) {
+    const int dxm = x == 0 ? k.nx - 1 : -1;
+    const int dxp = x == k.nx - 1 ? 1 - k.nx : 1;
+    const int dym = y == 0 ? (k.ny - 1) * k.pitch : -k.pitch;
+    const int dyp = y == k.ny - 1 ? (1 - k.ny) * k.pitch : k.pitch;
+    const int o[9] = {0, dxm, dym, dxp, dyp, dxm + dym, dxp + dym, dxp + dyp, dxm + dyp};
+    const int pl = k.plane32;
+    const int at = y * k.pitch + x;
+    const S* __restrict__ c = src + at;
+    const float sc = k.scale;
+    R f[9], h[9];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) f[i] = load_pop<S, R>(c + ((i - 1) * pl + o[i]), sc);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = load_pop<S, R>(c + ((8 + i) * pl + o[i]), sc);
+
+    // moments (Sec. 3.1-3.3)
+    const R sh = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+    const R th = (sh + R(0.5) * k.Q) * k.inv_sigma;
+    const R T = k.T0 + th;
+    const R a13 = f[1] + f[3], a24 = f[2] + f[4], d58 = (f[5] + f[7]) + (f[6] + f[8]);
+    const R sf = a13 + a24 + d58;
+    const R mx = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
+    const R my = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+    const R Pxx = a13 + d58, Pyy = a24 + d58;
+    const R Pxy = (f[5] + f[7]) - (f[6] + f[8]);
+    const R Gy = k.gbeta * th + k.ay;
+    const R vx = mx * k.inv_rho0 + k.half_eps_ax;
+    const R vy = my * k.inv_rho0 + k.half_eps * Gy;
+    const R vmag = sqrt(vx * vx + vy * vy);
+    const R iden = R(1) / (k.c0 + sqrt(k.c0sq + k.c1 * vmag));
+    const R ux = vx * iden, uy = vy * iden;
+    if (!isfinite(th + ux + uy)) atomicOr(k.flag, 1);
+    const R uu = ux * ux + uy * uy;
+    const R drag = k.e_nuK + k.e_FK * sqrt(uu);
+    const R Fx = k.eps * k.ax - drag * ux;
+    const R Fy = k.eps * Gy - drag * uy;
+    const R uF = ux * Fx + uy * Fy;
+    const R p = k.p_pref * sf - k.p_uF * uF - k.p_uu * uu;
+    const R ep = k.eps * p;
+    const R re = k.rho0 * k.inv_eps;
+    const R Sxx = (Pxx - ep + re * ux * (Fx - ux)) * k.invD;
+    const R Syy = (Pyy - ep + re * uy * (Fy - uy)) * k.invD;
+    const R Sxy = (Pxy + re * (R(0.5) * (ux * Fy + Fx * uy) - ux * uy)) * k.invD;
+    const R hx = (h[1] - h[3]) + (h[5] - h[7]) + (h[8] - h[6]);
+    const R hy = (h[2] - h[4]) + (h[5] - h[7]) + (h[6] - h[8]);
+    const R qs = R(0.5) * k.Q * k.inv_sigma;
+    const R Nx = hx + T * (R(0.5) * Fx - ux) + qs * ux;
+    const R Ny = hy + T * (R(0.5) * Fy - uy) + qs * uy;
+    const R a = k.a_const - R(0.5) * ep * k.inv_rho0;
+    const R ia = R(1) / a;
+    const R t = k.bcoef * (ux * Nx + uy * Ny) / (a - k.bcoef * uu);
+    const R gx = (Nx + t * ux) * ia;
+    const R gy = (Ny + t * uy) * ia;
+
+    // collision, pairs of opposite directions
+    const R EF0 = k.fA_ep * ep - k.fA_uu * uu - k.fA_tr * (Sxx + Syy) - k.fA_uF * uF;
+    const R EH0 = k.h_sig * th - k.h_uu * T * uu + k.h_pT * T * ep + k.h_kQ;
+    const R Kc = k.h_cu2 * T;
+    const R Ku = k.h_u3 * T + k.h_ug * (ux * gx + uy * gy) + k.h_uQ;
+    const R epr = ep * k.inv_rho0;
+    const R Wx = T * Fx + epr * gx, Wy = T * Fy + epr * gy;
+    R fo[9], ho[9];
+    auto pair = [&](int i, int j, R w, R cu, R cF, R ScS, R cg, R cW) {
+        const R evF = EF0 + k.f_cu2 * cu * cu + k.f_ScS * ScS + k.f_cucF * cu * cF;
+        const R odF = k.f_cu * cu + k.f_cF * cF;
+        fo[i] = k.omf * f[i] + w * (evF + odF);
+        fo[j] = k.omf * f[j] + w * (evF - odF);
+        const R evH = EH0 + Kc * cu * cu;
+        const R odH = Ku * cu + k.h_g * cg + k.h_W * cW;
+        ho[i] = k.omT * h[i] + w * (evH + odH);
+        ho[j] = k.omT * h[j] + w * (evH - odH);
+    };
+    const R w1 = R(1) / R(9), w5 = R(1) / R(36);
+    pair(1, 3, w1, ux, Fx, Sxx, gx, Wx);
+    pair(2, 4, w1, uy, Fy, Syy, gy, Wy);
+    pair(5, 7, w5, ux + uy, Fx + Fy, Sxx + Syy + R(2) * Sxy, gx + gy, Wx + Wy);
+    pair(6, 8, w5, uy - ux, Fy - Fx, Sxx + Syy - R(2) * Sxy, gy - gx, Wy - Wx);
+    ho[0] = k.omT * h[0] + (k.h0_sig * th - k.h0_uu * T * uu - k.h0_pT * T * ep + k.h0_kQ);
+
+    S* __restrict__ d = dst + at;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) store_pop<S, R>(d + (i - 1) * pl, fo[i], sc);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) store_pop<S, R>(d + (8 + i) * pl, ho[i], sc);
 }
 
 }  // namespace lbm

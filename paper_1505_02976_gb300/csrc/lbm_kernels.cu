@@ -1,10 +1,10 @@
 // lbm_kernels.cu -- the fused step kernel and the small auxiliary kernels.
 //
 // k_step: one thread per node, pull streaming from the ping buffer, all the
-// per-node arithmetic of the step in registers, NEES wall rebuild fused in
-// (the wall thread pulls its x_f neighbour's populations instead of its own,
-// so every thread runs the same moment code; only the collision differs), and
-// one write of the 17 post-collision planes to the pong buffer.
+// per-node arithmetic of the step in registers, and one write of the 17
+// post-collision planes to the pong buffer.  Wall nodes take the NEES rebuild
+// inside the same launch (an out-of-line path that pulls the populations of
+// the wall node's fluid neighbour x_f instead of its own).
 #include <math.h>
 
 #include "lbm_internal.h"
@@ -12,6 +12,11 @@
 namespace lbm {
 
 constexpr int kStepBlock = 128;
+// Resident blocks per SM the step kernel is compiled for: 8 x 128 threads
+// caps the FP32 kernel at 64 registers; the FP64 kernel keeps room to avoid
+// spilling.
+template <class R> struct StepOccupancy { static constexpr int blocks = 8; };
+template <> struct StepOccupancy<double> { static constexpr int blocks = 3; };
 
 template <class R, class S>
 __device__ __forceinline__ void store_node(const KConst<R>& k, S* __restrict__ dst, long long at,
@@ -32,43 +37,56 @@ __device__ __forceinline__ NodeState<R> target_state(const KConst<R>& k, const S
     return wall_state(k, w, s, thff);
 }
 
+// Wall node of one step: pull x_f's populations, its moments, the NEES
+// rebuild (Eqs. NEESVel, TNEESAp, TNEESApGra) and the collision with the
+// boundary equilibrium:
+//   f* = f^eq(x_b) + (1 - 1/tau)[f(x_f) - f^eq(x_f)] + F_i(x_b)   (same for g).
+// Kept out of line: only the 4(N - 1) wall threads take it.
 template <class R, class S>
-__global__ void __launch_bounds__(kStepBlock)
-k_step(const __grid_constant__ KConst<R> k, const S* __restrict__ src, S* __restrict__ dst) {
-    const int x = blockIdx.x * kStepBlock + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= k.nx) return;
+__device__ __noinline__ void wall_update(const KConst<R>& k, const S* __restrict__ src,
+                                         S* __restrict__ dst, int x, int y) {
     const WallInfo w = classify(k, x, y);
     Pops<R> P;
-    pull(k, src, w.wall ? w.xs : x, w.wall ? w.ys : y, P);
+    pull(k, src, w.xs, w.ys, P);
     const NodeState<R> s = node_moments(k, P);
     if (!(isfinite(s.th) && isfinite(s.ux) && isfinite(s.uy))) atomicOr(k.flag, 1);
     EqTerms<R> e;
     eq_terms(k, s, e);
+    R nf[9], nh[9];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) nf[i] = P.f[i] - e.fe[i];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) nh[i] = P.h[i] - e.he[i];
+    const NodeState<R> b = target_state(k, src, w, s);
+    EqTerms<R> eb;
+    eq_terms(k, b, eb);
     R fo[9], ho[9];
-    if (!w.wall) {
-        // BGK collision, Eqs. (LBEeq), (TEqColli)
 #pragma unroll
-        for (int i = 1; i < 9; ++i) fo[i] = e.fe[i] + k.omf * (P.f[i] - e.fe[i]) + e.Fi[i];
+    for (int i = 1; i < 9; ++i) fo[i] = eb.fe[i] + k.omf * nf[i] + eb.Fi[i];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) ho[i] = e.he[i] + k.omT * (P.h[i] - e.he[i]) + e.PQ[i];
-    } else {
-        // NEES rebuild (Eqs. NEESVel, TNEESAp) followed by the collision with
-        // the boundary equilibrium: f* = f^eq(x_b) + (1 - 1/tau)[f(x_f) - f^eq(x_f)] + F_i(x_b)
-        R nf[9], nh[9];
-#pragma unroll
-        for (int i = 1; i < 9; ++i) nf[i] = P.f[i] - e.fe[i];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) nh[i] = P.h[i] - e.he[i];
-        const NodeState<R> b = target_state(k, src, w, s);
-        EqTerms<R> eb;
-        eq_terms(k, b, eb);
-#pragma unroll
-        for (int i = 1; i < 9; ++i) fo[i] = eb.fe[i] + k.omf * nf[i] + eb.Fi[i];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) ho[i] = eb.he[i] + k.omT * nh[i] + eb.PQ[i];
-    }
+    for (int i = 0; i < 9; ++i) ho[i] = eb.he[i] + k.omT * nh[i] + eb.PQ[i];
     store_node(k, dst, (long long)y * k.pitch + x, fo, ho);
+}
+
+template <class R>
+__device__ __forceinline__ bool is_wall(const KConst<R>& k, int x, int y) {
+    return (x == 0 && k.bc[SW] != BC_PERIODIC) || (x == k.nx - 1 && k.bc[SE] != BC_PERIODIC) ||
+           (y == 0 && k.bc[SS] != BC_PERIODIC) || (y == k.ny - 1 && k.bc[SN] != BC_PERIODIC);
+}
+
+// The fused step: one thread per node; interior nodes take the fast path,
+// wall nodes the NEES path.
+template <class R, class S>
+__global__ void __launch_bounds__(kStepBlock, StepOccupancy<R>::blocks)
+k_step(const __grid_constant__ KConst<R> k, const S* __restrict__ src, S* __restrict__ dst) {
+    const int x = blockIdx.x * kStepBlock + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= k.nx) return;
+    if (is_wall(k, x, y)) {
+        wall_update(k, src, dst, x, y);
+        return;
+    }
+    interior_update(k, src, dst, x, y);
 }
 
 template <class R, class S>
