@@ -165,6 +165,20 @@ lbm_status lbm_moments(lbm_handle* h, double* p, double* ux, double* uy,
  * values, in host memory.  Synchronises. */
 lbm_status lbm_nusselt(lbm_handle* h, int side, double* nu_mean, double* nu_local);
 
+/* Mean Nusselt number of one wall, as lbm_nusselt computes it, for callers
+ * that must not allocate device memory (a program that reserves its whole
+ * device budget itself, a plugin that may not grow its host's footprint, a
+ * loop that cannot take the device-wide synchronisation of cudaMalloc).
+ * The paper has no counterpart to this entry point.  It allocates nothing:
+ * the per-node values live in a fixed array compiled into the library (held
+ * on every GPU that loads it until exit), so the wall may have at most 65536
+ * nodes (else LBM_ERR_ARG).  The first call on a device looks up that
+ * array's device address; make that first call before any stream capture.
+ * All calls share the array: calls whose GPU work overlaps (other streams or
+ * other handles on the same device) race.  nu_mean: host pointer.
+ * Synchronises the handle's stream. */
+lbm_status lbm_nusselt_noalloc(lbm_handle* h, int side, double* nu_mean);
+
 /* Steady-state criterion of Sec. 4 against the snapshot taken by the
  * previous lbm_residual call (or lbm_set_fields):
  *   res_u = sum |u - u_old|_2 / sum |u|_2,  res_T = sum |T - T_old| / sum |T|,

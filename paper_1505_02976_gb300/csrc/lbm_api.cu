@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <type_traits>
 #include <string>
@@ -542,3 +543,77 @@ int64_t lbm_steps_done(const lbm_handle* h) { return h ? h->steps : -1; }
 int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : -1; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Mean Nusselt number without any allocation (lbm_nusselt_noalloc).
+//
+// Some programs cannot let a library call cudaMalloc: a host application that
+// reserves its whole device-memory budget at start-up and hands out slices
+// of it, a plugin that must not grow the memory footprint of the process that
+// loads it, or a loop that cannot afford the device-wide synchronisation a
+// cudaMalloc/cudaFree implies.  Such a caller creates the handle on a
+// workspace of its own (lbm_create with a non-NULL workspace) and reads the
+// wall's mean Nusselt number with lbm_nusselt_noalloc, which keeps the
+// per-node values in the fixed array below instead of in the workspace.
+//
+// The array is compiled into the library: every GPU that loads the library
+// holds it until the process exits.  Its largest wall is kNoAllocMaxNodes
+// nodes; one slot after them holds the mean.  Nothing in it needs to start at
+// zero: each call writes all the per-node values it reads and the mean.  All
+// calls share it and it keeps the last call's values, so two calls whose GPU
+// work overlaps (different streams, or different handles on one device)
+// race on it.
+static constexpr int kNoAllocMaxNodes = 65536;
+static __device__ __align__(256) double g_nu_scratch[kNoAllocMaxNodes + 32];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_nu_scratch_mu;
+double* g_nu_scratch_ptr[kMaxDevices];  // device address of the array, per device
+
+// Device address of the scratch array on `device`, looked up once per device
+// with that device current.  In host code g_nu_scratch names a host-side
+// stand-in, not device memory; only this address may be given to a kernel.
+lbm_status nu_scratch_on(lbm_handle* h, int device, double** out) {
+    if (device < 0 || device >= kMaxDevices) return fail(h, LBM_ERR_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_nu_scratch_mu);
+    if (!g_nu_scratch_ptr[device]) {
+        int prev = -1;
+        LBM_CUDA(h, cudaGetDevice(&prev), "current device");
+        if (prev != device) LBM_CUDA(h, cudaSetDevice(device), "select the stream's device");
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_nu_scratch);
+        if (prev != device) cudaSetDevice(prev);
+        if (e != cudaSuccess) return cuda_fail(h, e, "address of the static Nusselt scratch");
+        g_nu_scratch_ptr[device] = (double*)p;
+    }
+    *out = g_nu_scratch_ptr[device];
+    return LBM_OK;
+}
+}  // namespace
+
+extern "C" lbm_status lbm_nusselt_noalloc(lbm_handle* h, int side, double* nu_mean) {
+    if (!h) return LBM_ERR_ARG;
+    if (side < 0 || side > 3 || !nu_mean) return fail(h, LBM_ERR_ARG, "bad side or null output");
+    const int n = side <= 1 ? h->prm.ny : h->prm.nx;
+    const int across = side <= 1 ? h->prm.nx : h->prm.ny;
+    if (across < 3) return fail(h, LBM_ERR_ARG, "the one-sided difference needs 3 nodes");
+    if (n > kNoAllocMaxNodes)
+        return fail(h, LBM_ERR_ARG,
+                    "wall longer than the 65536 nodes the static scratch of lbm_nusselt_noalloc holds");
+    int device = 0;
+    LBM_CUDA(h, cudaStreamGetDevice(h->stream, &device), "device of the handle's stream");
+    double* scratch = nullptr;
+    lbm_status s = nu_scratch_on(h, device, &scratch);
+    if (s != LBM_OK) return s;
+    double* mean = scratch + kNoAllocMaxNodes;
+    cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        return lbm::launch_nusselt(k, h->diag, (const S*)h->buf(h->cur), side, scratch, mean, h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "nusselt kernels");
+    LBM_CUDA(h, cudaMemcpyAsync(nu_mean, mean, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+             "nusselt copy");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "nusselt");
+    return LBM_OK;
+}
