@@ -213,6 +213,53 @@ def run_reference(args):
 
 # ----------------------------------------------------------------- GPU leg
 
+def time_steps(lat, stream, steps: int):
+    """Mean kernel time (event pair around each launch) and loop time (s)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for s0, s1 in ev:
+        s0.record(stream)
+        lat.step(1)
+        s1.record(stream)
+    b.record(stream)
+    b.synchronize()
+    kernel = sum(s0.elapsed_time(s1) for s0, s1 in ev) / 1e3 / steps
+    return kernel, a.elapsed_time(b) / 1e3
+
+
+def variant_lines(device, local, warmup: int, steps: int) -> dict:
+    """The reduced- and full-precision forms of the same step on this GPU:
+    FP16 storage at 8192 x 8192 (Ra 1e5, Da 1e-3, eps 0.6) and FP64 at
+    2048 x 2048 (the benchmark's groups)."""
+    import torch
+
+    from paper_1505_02976_gb300 import lbm
+    from paper_1505_02976_gb300 import workloads as W
+    out = {}
+    peak, _ = measured_peak_gbs()
+    for name, prec, p in (
+            ("cavity8192_fp16", "f16", W.cavity(8192, 1e5, 1e-3, 0.6)),
+            ("cavity2048_fp64", "f64", W.cavity(WORKLOAD["n"], WORKLOAD["Ra"], WORKLOAD["Da"], WORKLOAD["eps"]))):
+        stream = torch.cuda.Stream(device)
+        lat = lbm.Lattice(p, prec, device=local, stream=stream)
+        lat.step(warmup)
+        lat.sync()
+        kernel, loop = time_steps(lat, stream, steps)
+        lat.sync()
+        cells = p["nx"] * p["ny"]
+        gbs = BYTES_PER_CELL[prec] * cells / kernel / 1e9
+        out[name] = {"value": cells * steps / loop / 1e6, "unit": "MLUPS", "dtype": prec,
+                     "ms_per_step": 1e3 * loop / steps, "kernel_ms": 1e3 * kernel,
+                     "hbm_gbs": gbs, "hbm_frac": gbs / peak,
+                     "bytes_per_node": BYTES_PER_CELL[prec]}
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -293,6 +340,8 @@ def run_ours(args):
     achieved = algo_bytes / kernel_s / 1e9
     traffic = ncu_traffic_per_launch()
 
+    variants = variant_lines(device, local, 5, 30) if not args.no_variants else None
+
     out = None
     if rank == 0:
         cpu = cpu_baseline_leg() if world == 1 and not args.no_cpu_baseline else None
@@ -316,6 +365,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h / args.steps, "nu_hot": nu_mean.value},
             "gpu_launches": launches,
             "clocks": clk,
+            "variants": variants,
         }
         print(json.dumps(out), flush=True)
     lat.close()
@@ -332,6 +382,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP16 / FP64 comparison lines")
     ap.add_argument("--n", type=int, default=None,
                     help="lattice size override (profiling captures only; changes the workload)")
     args = ap.parse_args(argv)

@@ -193,8 +193,9 @@ class Oracle:
         self.steps = 0
 
     @classmethod
-    def from_state(cls, p: dict, f, g, eps_field=None):
-        """An oracle lattice holding the given post-collision populations."""
+    def from_state(cls, p: dict, f, g, eps_field=None, copy: bool = True):
+        """An oracle lattice holding the given post-collision populations
+        (copy=False adopts contiguous float64 arrays without copying)."""
         o = cls.__new__(cls)
         o.p = dict(p)
         o.s = problem_struct(p)
@@ -202,7 +203,11 @@ class Oracle:
         o.eps_field = _c64(eps_field)
         o.steps = 0
         derived(p)  # validates the problem
-        o.set_state(f, g)
+        if copy:
+            o.set_state(f, g)
+        else:
+            o.f = np.ascontiguousarray(f, dtype=np.float64)
+            o.g = np.ascontiguousarray(g, dtype=np.float64)
         return o
 
     def set_state(self, f, g):

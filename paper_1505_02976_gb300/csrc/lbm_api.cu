@@ -169,6 +169,7 @@ lbm::KConst<R> make_kconst(const lbm_params* p, const Derived& d, const Layout& 
         k.u_bc[s][1] = R(p->u_bc[s][1]);
     }
     k.scale = p->precision == LBM_F16 ? ldexpf(1.0f, -10) : 1.0f;
+    k.inv_scale = 1.0f / k.scale;
     k.flag = flag;
     k.plane32 = (int)L.plane_elems;
     // interior fast path: h* = (1 - 1/tau) h + [h^eq / tau + source], split
@@ -416,7 +417,7 @@ lbm_status lbm_step(lbm_handle* h, int64_t n) {
         const int src = h->cur, dst = 1 - h->cur;
         cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
             using S = std::remove_pointer_t<decltype(tag)>;
-            return lbm::launch_step(k, (const S*)h->buf(src), (S*)h->buf(dst), h->stream);
+            return lbm::launch_step(k, (const S*)h->buf(src), (S*)h->buf(dst), (uint32_t)h->steps, h->stream);
         });
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
         h->cur = dst;

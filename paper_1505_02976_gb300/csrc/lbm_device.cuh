@@ -29,6 +29,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbm {
 
 // D2Q9 in the paper's order (Sec. 3.1).
@@ -66,6 +68,7 @@ struct KConst {
     R T_bc[4];
     R u_bc[4][2];
     float scale;           // FP16 storage: stored value = population / scale
+    float inv_scale;       // 1 / scale (a power of two)
     int* flag;             // non-finite flag (device)
     int plane32;           // plane stride as a 32-bit offset (17 planes < 2^31 elements)
     // constants of the interior fast path (see interior_update)
@@ -87,6 +90,73 @@ __device__ __forceinline__ void store_pop(S* p, R v, float) { *p = S(v); }
 template <>
 __device__ __forceinline__ void store_pop<__half, float>(__half* p, float v, float scale) {
     *p = __float2half_rn(v / scale);
+}
+
+// Stochastic rounding of FP16 stores.  Near a steady state the same value
+// rounds the same way step after step, so round-to-nearest acts as a
+// persistent source of heat and momentum at every node (larger than the
+// buoyancy force per step at these Mach numbers).  Rounding up with
+// probability equal to the discarded fraction keeps every stored value exact
+// in expectation.  The random bits are counter based: the 32-bit integer hash
+// "lowbias32" (constants from C. Wellons' hash prospector) of the node index
+// and the step number seeds a Marsaglia xorshift32 sequence; each 32-bit draw
+// dithers two stored values with 13 bits each (the FP32 mantissa bits below
+// the FP16 mantissa).
+struct Dither {
+    uint32_t s;
+    __device__ __forceinline__ Dither(uint32_t node, uint32_t step) {
+        uint32_t x = node ^ (step * 0x9E3779B9u);
+        x ^= x >> 16;
+        x *= 0x7feb352du;
+        x ^= x >> 15;
+        x *= 0x846ca68bu;
+        x ^= x >> 16;
+        s = x | 1u;  // xorshift32 needs a non-zero state
+    }
+    __device__ __forceinline__ uint32_t next() {
+        s ^= s << 13;
+        s ^= s >> 17;
+        s ^= s << 5;
+        return s;
+    }
+};
+
+// v (already divided by the storage scale) rounded to FP16 stochastically:
+// add 13 random bits below FP16's last mantissa bit, then truncate.
+__device__ __forceinline__ __half half_sr(float v, uint32_t r) {
+    return __float2half_rz(__uint_as_float(__float_as_uint(v) + (r & 0x1FFFu)));
+}
+
+// Store of the 17 post-collision values of one node; FP16 storage rounds
+// stochastically (dither != nullptr) or to nearest.
+template <class S, class R>
+__device__ __forceinline__ void store_planes(S* __restrict__ d, long long pl, const R* fo, const R* ho,
+                                             float inv_scale, Dither* dither) {
+    if constexpr (std::is_same<S, __half>::value) {
+        if (dither) {
+            uint32_t r = 0;
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                r = (i & 1) ? dither->next() : (r >> 16);
+                d[(i - 1) * pl] = half_sr(float(fo[i]) * inv_scale, r);
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                r = (i & 1) ? (r >> 16) : dither->next();
+                d[(8 + i) * pl] = half_sr(float(ho[i]) * inv_scale, r);
+            }
+            return;
+        }
+#pragma unroll
+        for (int i = 1; i < 9; ++i) d[(i - 1) * pl] = __float2half_rn(float(fo[i]) * inv_scale);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[(8 + i) * pl] = __float2half_rn(float(ho[i]) * inv_scale);
+    } else {
+#pragma unroll
+        for (int i = 1; i < 9; ++i) d[(i - 1) * pl] = S(fo[i]);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[(8 + i) * pl] = S(ho[i]);
+    }
 }
 
 // Plane k of the stored state: k = 0..7 hold f_1..f_8, k = 8..16 hold h_0..h_8.
@@ -318,7 +388,7 @@ __device__ __forceinline__ NodeState<R> wall_state(const KConst<R>& k, const Wal
 //    c_i -> -c_i, so each pair of opposite directions shares one evaluation.
 template <class R, class S>
 __device__ __forceinline__ void interior_update(const KConst<R>& k, const S* __restrict__ src,
-                                                S* __restrict__ dst, int x, int y) {
+                                                S* __restrict__ dst, int x, int y, uint32_t step) {
     const int dxm = x == 0 ? k.nx - 1 : -1;
     const int dxp = x == k.nx - 1 ? 1 - k.nx : 1;
     const int dym = y == 0 ? (k.ny - 1) * k.pitch : -k.pitch;
@@ -398,11 +468,8 @@ __device__ __forceinline__ void interior_update(const KConst<R>& k, const S* __r
     pair(6, 8, w5, uy - ux, Fy - Fx, Sxx + Syy - R(2) * Sxy, gy - gx, Wy - Wx);
     ho[0] = k.omT * h[0] + (k.h0_sig * th - k.h0_uu * T * uu - k.h0_pT * T * ep + k.h0_kQ);
 
-    S* __restrict__ d = dst + at;
-#pragma unroll
-    for (int i = 1; i < 9; ++i) store_pop<S, R>(d + (i - 1) * pl, fo[i], sc);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) store_pop<S, R>(d + (8 + i) * pl, ho[i], sc);
+    Dither dither((uint32_t)at, step);
+    store_planes<S, R>(dst + at, pl, fo, ho, k.inv_scale, &dither);
 }
 
 }  // namespace lbm

@@ -14,8 +14,10 @@ struct DiagConst {
     double T_bc[4];
 };
 
+// One time step from src to dst; step seeds the stochastic rounding of FP16
+// storage (unused otherwise).
 template <class R, class S>
-cudaError_t launch_step(const KConst<R>& k, const S* src, S* dst, cudaStream_t st);
+cudaError_t launch_step(const KConst<R>& k, const S* src, S* dst, uint32_t step, cudaStream_t st);
 
 template <class R, class S>
 cudaError_t launch_init(const KConst<R>& k, S* dst, const double* T, const double* ux,

@@ -20,11 +20,8 @@ template <> struct StepOccupancy<double> { static constexpr int blocks = 3; };
 
 template <class R, class S>
 __device__ __forceinline__ void store_node(const KConst<R>& k, S* __restrict__ dst, long long at,
-                                           const R* fo, const R* ho) {
-#pragma unroll
-    for (int i = 1; i < 9; ++i) store_pop<S, R>(dst + (long long)(i - 1) * k.plane + at, fo[i], k.scale);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) store_pop<S, R>(dst + (long long)(8 + i) * k.plane + at, ho[i], k.scale);
+                                           const R* fo, const R* ho, Dither* dither = nullptr) {
+    store_planes<S, R>(dst + at, k.plane, fo, ho, k.inv_scale, dither);
 }
 
 // Boundary state of a wall node, or the node's own state.
@@ -44,7 +41,7 @@ __device__ __forceinline__ NodeState<R> target_state(const KConst<R>& k, const S
 // Kept out of line: only the 4(N - 1) wall threads take it.
 template <class R, class S>
 __device__ __noinline__ void wall_update(const KConst<R>& k, const S* __restrict__ src,
-                                         S* __restrict__ dst, int x, int y) {
+                                         S* __restrict__ dst, int x, int y, uint32_t step) {
     const WallInfo w = classify(k, x, y);
     Pops<R> P;
     pull(k, src, w.xs, w.ys, P);
@@ -65,7 +62,8 @@ __device__ __noinline__ void wall_update(const KConst<R>& k, const S* __restrict
     for (int i = 1; i < 9; ++i) fo[i] = eb.fe[i] + k.omf * nf[i] + eb.Fi[i];
 #pragma unroll
     for (int i = 0; i < 9; ++i) ho[i] = eb.he[i] + k.omT * nh[i] + eb.PQ[i];
-    store_node(k, dst, (long long)y * k.pitch + x, fo, ho);
+    Dither dither((uint32_t)(y * k.pitch + x), step);
+    store_node(k, dst, (long long)y * k.pitch + x, fo, ho, &dither);
 }
 
 template <class R>
@@ -78,15 +76,15 @@ __device__ __forceinline__ bool is_wall(const KConst<R>& k, int x, int y) {
 // wall nodes the NEES path.
 template <class R, class S>
 __global__ void __launch_bounds__(kStepBlock, StepOccupancy<R>::blocks)
-k_step(const __grid_constant__ KConst<R> k, const S* __restrict__ src, S* __restrict__ dst) {
+k_step(const __grid_constant__ KConst<R> k, const S* __restrict__ src, S* __restrict__ dst, uint32_t step) {
     const int x = blockIdx.x * kStepBlock + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= k.nx) return;
     if (is_wall(k, x, y)) {
-        wall_update(k, src, dst, x, y);
+        wall_update(k, src, dst, x, y, step);
         return;
     }
-    interior_update(k, src, dst, x, y);
+    interior_update(k, src, dst, x, y, step);
 }
 
 template <class R, class S>
@@ -276,8 +274,8 @@ long long residual_blocks(int nx, int ny) {
 }
 
 template <class R, class S>
-cudaError_t launch_step(const KConst<R>& k, const S* src, S* dst, cudaStream_t st) {
-    k_step<R, S><<<row_grid(k.nx, k.ny, kStepBlock), kStepBlock, 0, st>>>(k, src, dst);
+cudaError_t launch_step(const KConst<R>& k, const S* src, S* dst, uint32_t step, cudaStream_t st) {
+    k_step<R, S><<<row_grid(k.nx, k.ny, kStepBlock), kStepBlock, 0, st>>>(k, src, dst, step);
     return cudaGetLastError();
 }
 
@@ -331,7 +329,7 @@ cudaError_t launch_residual(const KConst<R>& k, const S* src, double* snap, doub
 }
 
 #define LBM_INSTANTIATE(R, S)                                                                        \
-    template cudaError_t launch_step<R, S>(const KConst<R>&, const S*, S*, cudaStream_t);           \
+    template cudaError_t launch_step<R, S>(const KConst<R>&, const S*, S*, uint32_t, cudaStream_t);           \
     template cudaError_t launch_init<R, S>(const KConst<R>&, S*, const double*, const double*,      \
                                            const double*, double, cudaStream_t);                    \
     template cudaError_t launch_moments<R, S>(const KConst<R>&, const S*, double*, double*, double*, \

@@ -210,3 +210,54 @@ def test_nonfinite_input_is_reported():
     g.set_fields()
     g.step(2)
     g.sync()
+
+
+def test_fp16_cavity_against_oracle():
+    """FP16 storage (stochastic rounding), FP32 arithmetic: 64 x 64 cavity at
+    the FP16 benchmark's groups (Ra 1e5, Da 1e-3, eps 0.6), 2000 steps.
+    Bounds: max abs dT <= 3e-3, L2(du)/L2(u) <= 3e-3, abs dNu / Nu <= 3e-3."""
+    p = W.cavity(64, 1e5, 1e-3, 0.6)
+    o, g = _pair(p, "f16", steps=2000)
+    mo, mg = o.moments(), g.moments()
+    assert np.abs(mg["T"] - mo["T"]).max() <= 3e-3
+    du = np.sqrt((mg["ux"] - mo["ux"]) ** 2 + (mg["uy"] - mo["uy"]) ** 2)
+    un = np.sqrt(mo["ux"] ** 2 + mo["uy"] ** 2)
+    assert np.linalg.norm(du) / np.linalg.norm(un) <= 3e-3
+    a, _ = g.nusselt("W")
+    b, _ = o.nusselt("W")
+    assert abs(a - b) <= 3e-3 * abs(b)
+
+
+def test_fp16_one_step_sampled_at_full_size():
+    """The 8192 x 8192 FP16 workload: one step from a developed state, sampled
+    nodes against the oracle's node update on the same FP16-stored state.
+    The GPU output is rounded to FP16 stochastically, so each value may differ
+    by one FP16 step of its magnitude (2^-10 relative) plus FP32 rounding."""
+    n = 8192
+    p = W.cavity(n, 1e5, 1e-3, 0.6)
+    g = lbm.Lattice(p, "f16")
+    g.set_fields(*W.random_fields(p, seed=31, amp_u=2e-3, amp_T=0.3))
+    g.step(5)
+    f0, g0 = g.get_state()
+    g.step(1)
+    f1, g1 = g.get_state()
+    f0[0] = 0.0
+    o = oracle.Oracle.from_state(p, f0, g0, copy=False)
+    rng = np.random.Generator(np.random.PCG64(12))
+    xs = np.r_[rng.integers(0, n, 400), 0, 0, n - 1, n - 1, 1, 2, n - 2].astype(np.int32)
+    ys = np.r_[rng.integers(0, n, 400), 0, n - 1, 0, n - 1, 0, n - 1, 1].astype(np.int32)
+    fo, go = o.update_nodes(xs, ys)
+    fg = f1[:, ys, xs].T
+    gg = g1[:, ys, xs].T
+    assert np.all(np.abs(fg[:, 1:] - fo[:, 1:]) <= 2.0 ** -10 * np.abs(fo[:, 1:]) + 1e-6 * np.abs(fo[:, 1:]).max())
+    # thermal populations are stored as deviations from w_i sigma T0
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    dev = np.abs(go - w * 0.5)
+    assert np.all(np.abs(gg - go) <= 2.0 ** -10 * dev + 1e-6 * dev.max())
+
+
+def test_fp16_halves_the_population_storage():
+    p = W.cavity(1024, 1e5, 1e-3, 0.6)
+    n16 = lbm.lbm_workspace_size(p, "f16")
+    n32 = lbm.lbm_workspace_size(p, "f32")
+    assert n32 - n16 >= 2 * 17 * 1024 * 1024 * 2
