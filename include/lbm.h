@@ -202,6 +202,70 @@ int64_t lbm_steps_done(const lbm_handle* h);
 /* Number of step-kernel launches issued by this handle so far. */
 int64_t lbm_kernel_launches(const lbm_handle* h);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent cavities of different size and parameters
+ * advanced together (the paper's cavity problem of Sec. 4.2 run for a set of
+ * (N, Ra, Da, eps) at once).  Each cavity is the lattice an lbm_params
+ * describes; all cavities of a batch share the storage precision (FP64 or
+ * FP32) and step together.  The state of every cavity starts at its uniform
+ * rest state.
+ * ---------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+
+typedef enum {
+    LBM_BATCH_FUSED = 0,     /* one kernel launch per step for all cavities */
+    LBM_BATCH_GRAPH = 1,     /* the same launches replayed from a captured CUDA graph
+                                (50 steps per graph; needs a non-default stream) */
+    LBM_BATCH_PER_CASE = 2   /* one single-lattice launch per cavity per step */
+} lbm_batch_mode;
+
+/* Bytes of device workspace for the n cavities of p[0..n-1]. */
+lbm_status lbm_batch_workspace_size(const lbm_params* p, int32_t n, size_t* bytes);
+
+/* Create a batch of the n cavities p[0..n-1] (same conventions as
+ * lbm_create: caller workspace or NULL for a library allocation). */
+lbm_status lbm_batch_create(const lbm_params* p, int32_t n, void* stream, void* workspace,
+                            size_t workspace_bytes, lbm_batch** out);
+
+void lbm_batch_destroy(lbm_batch* b);
+
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* Initialise cavity `cavity` from host fields [ny][nx] (NULL: T_init, 0, 0),
+ * as lbm_set_fields does; cavity = -1 resets every cavity to its rest state
+ * (fields must then be NULL) and the step counter.  Synchronises. */
+lbm_status lbm_batch_set_fields(lbm_batch* b, int32_t cavity, const double* T, const double* ux,
+                                const double* uy);
+
+/* Advance every cavity n steps in the given lbm_batch_mode.  Asynchronous. */
+lbm_status lbm_batch_step(lbm_batch* b, int64_t n, int mode);
+
+/* Pick the tile width (32, 64 or 128 nodes; tiles hold 128 nodes) and the
+ * grid size (1, 2 or 4 waves of resident blocks) of the fused step by timing
+ * steps_per_candidate + 1 steps of each candidate.  These are real steps of
+ * the run (every launch shape computes identical values).  Synchronises. */
+lbm_status lbm_batch_autotune(lbm_batch* b, int32_t steps_per_candidate, int32_t* tile_x, int32_t* grid);
+
+/* Set the fused step's launch shape explicitly. */
+lbm_status lbm_batch_set_launch(lbm_batch* b, int32_t tile_x, int32_t grid);
+
+/* Wait for the stream; LBM_ERR_NONFINITE if any cavity produced a NaN/Inf. */
+lbm_status lbm_batch_sync(lbm_batch* b);
+
+/* Mean Nusselt number of every cavity on one side (as lbm_nusselt), into
+ * nu_mean[n] in host memory.  Synchronises. */
+lbm_status lbm_batch_nusselt(lbm_batch* b, int side, double* nu_mean);
+
+/* Macroscopic fields of one cavity (as lbm_moments), host outputs.
+ * Synchronises. */
+lbm_status lbm_batch_moments(lbm_batch* b, int32_t cavity, double* p, double* ux, double* uy,
+                             double* T);
+
+int64_t lbm_batch_steps_done(const lbm_batch* b);
+
+/* Kernel launches issued for steps (a graph replay counts its 50 launches). */
+int64_t lbm_batch_kernel_launches(const lbm_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

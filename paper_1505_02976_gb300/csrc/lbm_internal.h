@@ -50,4 +50,36 @@ cudaError_t launch_residual(const KConst<R>& k, const S* src, double* snap, doub
 
 long long residual_blocks(int nx, int ny);
 
+// ---------------------------------------------------------------- batches
+// One cavity of a batch: its constants (pitch and plane relative to its own
+// planes) and the element offset of its first plane in the batch buffers.
+template <class R>
+struct BatchCavity {
+    KConst<R> k;
+    DiagConst d;
+    long long offset;
+};
+
+// Work item of the batched step: cavity index, tile origin x0, y0.
+struct BatchItem {
+    int cavity, x0, y0, pad;
+};
+
+// One time step of every cavity: the work list is split into equal
+// contiguous chunks, one per block of a grid of `grid` blocks; tiles are
+// tile_x x (128 / tile_x) nodes (tile_x in {32, 64, 128}).
+template <class R, class S>
+cudaError_t launch_step_batch(const BatchCavity<R>* cav, const BatchItem* items, int n_items,
+                              int tile_x, int grid, const S* src, S* dst, uint32_t step,
+                              cudaStream_t st);
+
+// Mean Nusselt number of every cavity on one side into out[c].
+template <class R, class S>
+cudaError_t launch_nusselt_batch(const BatchCavity<R>* cav, int n, const S* src, int side,
+                                 double* out, cudaStream_t st);
+
+// Resident blocks per SM of the batched step kernel.
+template <class R, class S>
+int batch_blocks_per_sm(int tile_x);
+
 }  // namespace lbm

@@ -347,4 +347,112 @@ LBM_INSTANTIATE(double, double)
 LBM_INSTANTIATE(float, float)
 LBM_INSTANTIATE(float, __half)
 
+// ------------------------------------------------------------------ batches
+
+// Batched step: a grid of resident blocks walks a work list of tiles drawn
+// from many cavities of different size and parameters.  Each block takes one
+// contiguous chunk of the list (items are sorted by cavity, so a block
+// changes cavity rarely) and stages the current cavity's constants in shared
+// memory; every node then runs the same interior / wall code as k_step.
+template <class R, class S, int TX>
+__global__ void __launch_bounds__(kStepBlock, StepOccupancy<R>::blocks)
+k_step_batch(const BatchCavity<R>* __restrict__ cav, const BatchItem* __restrict__ items, int n_items,
+             int per_block, const S* __restrict__ src, S* __restrict__ dst, uint32_t step) {
+    __shared__ KConst<R> ks;
+    __shared__ long long off;
+    constexpr int TY = kStepBlock / TX;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int begin = blockIdx.x * per_block;
+    const int end = min(begin + per_block, n_items);
+    int cur = -1;
+    for (int it = begin; it < end; ++it) {
+        const BatchItem w = items[it];
+        if (w.cavity != cur) {
+            __syncthreads();
+            const int* from = reinterpret_cast<const int*>(&cav[w.cavity].k);
+            int* to = reinterpret_cast<int*>(&ks);
+            for (int q = threadIdx.x; q < (int)(sizeof(KConst<R>) / sizeof(int)); q += kStepBlock) to[q] = from[q];
+            if (threadIdx.x == 0) off = cav[w.cavity].offset;
+            __syncthreads();
+            cur = w.cavity;
+        }
+        const int x = w.x0 + tx, y = w.y0 + ty;
+        (void)TY;
+        if (x < ks.nx && y < ks.ny) {
+            const S* s = src + off;
+            S* d = dst + off;
+            if (is_wall(ks, x, y)) wall_update(ks, s, d, x, y, step);
+            else interior_update(ks, s, d, x, y, step);
+        }
+    }
+}
+
+template <class R, class S>
+__global__ void k_nusselt_batch(const BatchCavity<R>* __restrict__ cav, const S* __restrict__ src,
+                                int side, double* __restrict__ out) {
+    __shared__ double sh[kReduceBlock / 32];
+    const BatchCavity<R>& c = cav[blockIdx.x];
+    const KConst<R>& k = c.k;
+    const S* s = src + c.offset;
+    const int n = side <= SE ? k.ny : k.nx;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < n; j += kReduceBlock) {
+        double t[3];
+        for (int m = 0; m < 3; ++m) {
+            int x, y;
+            if (side == SW) { x = m; y = j; }
+            else if (side == SE) { x = k.nx - 1 - m; y = j; }
+            else if (side == SS) { x = j; y = m; }
+            else { x = j; y = k.ny - 1 - m; }
+            t[m] = node_T(k, c.d, s, x, y);
+        }
+        const double d_in = (-3.0 * t[0] + 4.0 * t[1] - t[2]) * 0.5;
+        const double d_axis = (side == SW || side == SS) ? d_in : -d_in;
+        acc += ((j == 0 || j == n - 1) ? 0.5 : 1.0) * (-c.d.L * d_axis / c.d.dT);
+    }
+    const double total = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = total / double(n - 1);
+}
+
+template <class R, class S>
+cudaError_t launch_step_batch(const BatchCavity<R>* cav, const BatchItem* items, int n_items, int tile_x,
+                              int grid, const S* src, S* dst, uint32_t step, cudaStream_t st) {
+    if (grid < 1 || n_items < 1) return cudaErrorInvalidValue;
+    const int per_block = (n_items + grid - 1) / grid;
+    switch (tile_x) {
+    case 32: k_step_batch<R, S, 32><<<grid, kStepBlock, 0, st>>>(cav, items, n_items, per_block, src, dst, step); break;
+    case 64: k_step_batch<R, S, 64><<<grid, kStepBlock, 0, st>>>(cav, items, n_items, per_block, src, dst, step); break;
+    case 128: k_step_batch<R, S, 128><<<grid, kStepBlock, 0, st>>>(cav, items, n_items, per_block, src, dst, step); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <class R, class S>
+cudaError_t launch_nusselt_batch(const BatchCavity<R>* cav, int n, const S* src, int side, double* out,
+                                 cudaStream_t st) {
+    k_nusselt_batch<R, S><<<n, kReduceBlock, 0, st>>>(cav, src, side, out);
+    return cudaGetLastError();
+}
+
+template <class R, class S>
+int batch_blocks_per_sm(int tile_x) {
+    int b = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (tile_x == 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_batch<R, S, 32>, kStepBlock, 0);
+    if (tile_x == 64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_batch<R, S, 64>, kStepBlock, 0);
+    if (tile_x == 128) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_batch<R, S, 128>, kStepBlock, 0);
+    return e == cudaSuccess ? b : 0;
+}
+
+#define LBM_INSTANTIATE_BATCH(R, S)                                                                  \
+    template cudaError_t launch_step_batch<R, S>(const BatchCavity<R>*, const BatchItem*, int, int, \
+                                                 int, const S*, S*, uint32_t, cudaStream_t);        \
+    template cudaError_t launch_nusselt_batch<R, S>(const BatchCavity<R>*, int, const S*, int,      \
+                                                    double*, cudaStream_t);                         \
+    template int batch_blocks_per_sm<R, S>(int);
+
+LBM_INSTANTIATE_BATCH(double, double)
+LBM_INSTANTIATE_BATCH(float, float)
+
 }  // namespace lbm

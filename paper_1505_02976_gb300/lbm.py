@@ -26,7 +26,11 @@ SIDE = {"W": 0, "E": 1, "S": 2, "N": 3}
 EXPORTED = ("lbm_params_default", "lbm_derived", "lbm_workspace_size", "lbm_create", "lbm_destroy",
             "lbm_last_error", "lbm_set_fields", "lbm_step", "lbm_sync", "lbm_moments", "lbm_nusselt",
             "lbm_residual", "lbm_get_state", "lbm_set_state", "lbm_steps_done",
-            "lbm_kernel_launches")
+            "lbm_kernel_launches", "lbm_batch_workspace_size", "lbm_batch_create",
+            "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_set_fields", "lbm_batch_step",
+            "lbm_batch_autotune", "lbm_batch_set_launch", "lbm_batch_sync", "lbm_batch_nusselt",
+            "lbm_batch_moments", "lbm_batch_steps_done", "lbm_batch_kernel_launches")
+BATCH_MODE = {"fused": 0, "graph": 1, "per_case": 2}
 
 
 class LbmError(RuntimeError):
@@ -88,8 +92,28 @@ def load(build_if_missing: bool = True):
     L.lbm_steps_done.restype = C.c_int64
     L.lbm_kernel_launches.argtypes = [H]
     L.lbm_kernel_launches.restype = C.c_int64
+    B = C.c_void_p
+    L.lbm_batch_workspace_size.argtypes = [P, C.c_int32, C.POINTER(C.c_size_t)]
+    L.lbm_batch_create.argtypes = [P, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(B)]
+    L.lbm_batch_destroy.argtypes = [B]
+    L.lbm_batch_destroy.restype = None
+    L.lbm_batch_last_error.argtypes = [B]
+    L.lbm_batch_last_error.restype = C.c_char_p
+    L.lbm_batch_set_fields.argtypes = [B, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.lbm_batch_step.argtypes = [B, C.c_int64, C.c_int]
+    L.lbm_batch_autotune.argtypes = [B, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.lbm_batch_set_launch.argtypes = [B, C.c_int32, C.c_int32]
+    L.lbm_batch_sync.argtypes = [B]
+    L.lbm_batch_nusselt.argtypes = [B, C.c_int, C.c_void_p]
+    L.lbm_batch_moments.argtypes = [B, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.lbm_batch_steps_done.argtypes = [B]
+    L.lbm_batch_steps_done.restype = C.c_int64
+    L.lbm_batch_kernel_launches.argtypes = [B]
+    L.lbm_batch_kernel_launches.restype = C.c_int64
     for name in EXPORTED:
-        if name not in ("lbm_destroy", "lbm_last_error", "lbm_steps_done", "lbm_kernel_launches"):
+        if name not in ("lbm_destroy", "lbm_last_error", "lbm_steps_done", "lbm_kernel_launches",
+                        "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_steps_done",
+                        "lbm_batch_kernel_launches"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -245,6 +269,109 @@ class Lattice:
     @property
     def launches(self) -> int:
         return int(self.lib.lbm_kernel_launches(self.h))
+
+
+def _params_array(problems, precision):
+    arr = (lbm_params * len(problems))()
+    for k, p in enumerate(problems):
+        arr[k] = params_from_problem(p, precision)
+    return arr
+
+
+def lbm_batch_workspace_size(problems, precision: str = "f32") -> int:
+    n = C.c_size_t()
+    status = load().lbm_batch_workspace_size(_params_array(problems, precision), len(problems), C.byref(n))
+    if status != LBM_OK:
+        raise LbmError(status, load().lbm_batch_last_error(None).decode())
+    return int(n.value)
+
+
+class Batch:
+    """Many cavities advanced together (``lbm_batch_*``).  The stream must
+    not be the legacy default stream for graph mode; a private torch stream
+    is created when none is given."""
+
+    def __init__(self, problems, precision: str = "f32", device: int = 0, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise LbmError(-2, "no CUDA device: the library has no CPU path")
+        self.lib = load()
+        self.problems = [dict(p) for p in problems]
+        self.n = len(problems)
+        self.precision = precision
+        self.device = torch.device("cuda", device)
+        self.params = _params_array(problems, precision)
+        nbytes = lbm_batch_workspace_size(problems, precision)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        h = C.c_void_p()
+        status = self.lib.lbm_batch_create(self.params, self.n, C.c_void_p(self.stream.cuda_stream),
+                                           _ptr(self.workspace), nbytes, C.byref(h))
+        if status != LBM_OK:
+            raise LbmError(status, self.lib.lbm_batch_last_error(None).decode())
+        self.h = h
+
+    def _check(self, status):
+        if status != LBM_OK:
+            raise LbmError(status, self.lib.lbm_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_fields(self, cavity: int, T=None, ux=None, uy=None):
+        conv = lambda a: None if a is None else np.ascontiguousarray(a, np.float64)
+        T, ux, uy = conv(T), conv(ux), conv(uy)
+        self._check(self.lib.lbm_batch_set_fields(self.h, int(cavity), _ptr(T), _ptr(ux), _ptr(uy)))
+
+    def step(self, n: int = 1, mode: str = "fused"):
+        self._check(self.lib.lbm_batch_step(self.h, int(n), BATCH_MODE[mode]))
+
+    def autotune(self, steps_per_candidate: int = 3):
+        tx, grid = C.c_int32(), C.c_int32()
+        self._check(self.lib.lbm_batch_autotune(self.h, int(steps_per_candidate), C.byref(tx), C.byref(grid)))
+        return tx.value, grid.value
+
+    def set_launch(self, tile_x: int, grid: int):
+        self._check(self.lib.lbm_batch_set_launch(self.h, int(tile_x), int(grid)))
+
+    def sync(self):
+        self._check(self.lib.lbm_batch_sync(self.h))
+
+    def nusselt(self, side="W"):
+        k = SIDE[side] if isinstance(side, str) else int(side)
+        out = np.empty(self.n)
+        self._check(self.lib.lbm_batch_nusselt(self.h, k, _ptr(out)))
+        return out
+
+    def moments(self, cavity: int) -> dict:
+        p = self.problems[cavity]
+        shape = (int(p["ny"]), int(p["nx"]))
+        out = {k: np.empty(shape) for k in ("p", "ux", "uy", "T")}
+        self._check(self.lib.lbm_batch_moments(self.h, int(cavity), _ptr(out["p"]), _ptr(out["ux"]),
+                                               _ptr(out["uy"]), _ptr(out["T"])))
+        return out
+
+    @property
+    def steps(self) -> int:
+        return int(self.lib.lbm_batch_steps_done(self.h))
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.lbm_batch_kernel_launches(self.h))
+
+    @property
+    def cells(self) -> int:
+        return sum(int(p["nx"]) * int(p["ny"]) for p in self.problems)
 
 
 def mlups(nx: int, ny: int, steps: int, seconds: float) -> float:
