@@ -22,8 +22,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_CS_LIB_PATH = os.path.join(_OUT_DIR, "liboracle_cs.so")
 _lock = threading.Lock()
 _lib = None
+_cs_lib = None
 
 _BC = {"periodic": 0, "dirichlet": 1, "adiabatic": 2}
 SIDE = {"W": 0, "E": 1, "S": 2, "N": 3}
@@ -44,19 +46,27 @@ class _Problem(C.Structure):
     ]
 
 
+def _compile(out: str, extra=()) -> str:
+    if os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99", *extra,
+                    "-o", tmp, _SRC, "-lm"], check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into a shared library (plain gcc, -O2, no FMA
-    contraction, no target-specific flags)."""
+    contraction, no target-specific flags), and its complex-step twin."""
     with _lock:
-        if (not force and os.path.exists(_LIB_PATH)
-                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-            return _LIB_PATH
-        os.makedirs(_OUT_DIR, exist_ok=True)
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99",
-                        "-o", tmp, _SRC, "-lm"], check=True)
-        os.replace(tmp, _LIB_PATH)
-        return _LIB_PATH
+        if force:
+            for f in (_LIB_PATH, _CS_LIB_PATH):
+                if os.path.exists(f):
+                    os.remove(f)
+        _compile(_CS_LIB_PATH, ("-DORC_COMPLEX",))
+        return _compile(_LIB_PATH)
 
 
 def lib():
@@ -83,6 +93,73 @@ def lib():
         L.orc_totals.argtypes = [P, dp, dp, dp]
         _lib = L
     return _lib
+
+
+def cs_lib():
+    """The oracle compiled over complex numbers (complex-step derivatives)."""
+    global _cs_lib
+    if _cs_lib is None:
+        build()
+        L = C.CDLL(_CS_LIB_PATH)
+        cp = np.ctypeslib.ndpointer(dtype=np.complex128, flags="C_CONTIGUOUS")
+        dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+        P = C.POINTER(_Problem)
+        vp = C.c_void_p
+        L.orc_cs_set_tbc_imag.argtypes = [dp]
+        L.orc_init.argtypes = [P, vp, vp, vp, vp, cp, cp]
+        L.orc_run.argtypes = [P, vp, cp, cp, C.c_int64]
+        L.orc_moments.argtypes = [P, vp, cp, cp, vp, vp, vp, vp]
+        L.orc_nusselt.argtypes = [P, cp, C.c_int, vp, vp]
+        _cs_lib = L
+    return _cs_lib
+
+
+def complex_step_nusselt(p: dict, steps: int, eps_field=None, tbc_imag=(0.0, 0.0, 0.0, 0.0),
+                         T=None, ux=None, uy=None, side: str = "W"):
+    """Mean Nusselt number on `side` after `steps` steps, evaluated in
+    complex arithmetic.  eps_field may be complex (a perturbed cell carries
+    i h); tbc_imag adds i h to Dirichlet wall temperatures.  Returns the
+    complex Nu: its imaginary part / h is the exact discrete derivative."""
+    L = cs_lib()
+    s = problem_struct(p)
+    nx, ny = int(p["nx"]), int(p["ny"])
+    c = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.complex128)
+    eps_c = c(eps_field)
+    L.orc_cs_set_tbc_imag(np.ascontiguousarray(tbc_imag, dtype=np.float64))
+    f = np.zeros((9, ny, nx), np.complex128)
+    g = np.zeros((9, ny, nx), np.complex128)
+    rc = L.orc_init(C.byref(s), _ptr(c(T)), _ptr(c(ux)), _ptr(c(uy)), _ptr(eps_c), f, g)
+    if rc:
+        raise ValueError(f"oracle rejected the problem (code {rc})")
+    rc = L.orc_run(C.byref(s), _ptr(eps_c), f, g, int(steps))
+    if rc:
+        raise RuntimeError(f"oracle run failed (code {rc})")
+    Tf = np.zeros((ny, nx), np.complex128)
+    L.orc_moments(C.byref(s), _ptr(eps_c), f, g, None, None, None, _ptr(Tf))
+    mean = np.zeros(1, np.complex128)
+    L.orc_nusselt(C.byref(s), Tf, SIDE[side], None, _ptr(mean))
+    L.orc_cs_set_tbc_imag(np.zeros(4))
+    return complex(mean[0])
+
+
+def nusselt_gradient(p: dict, steps: int, eps_field, cells, sides=("W", "E"), h: float = 1e-30,
+                     T=None, ux=None, uy=None):
+    """Exact discrete derivatives of the hot-wall mean Nusselt number after
+    `steps` steps with respect to eps at each (x, y) in `cells` and to the
+    Dirichlet temperature of each side in `sides`, by the complex-step
+    method (one complex run per derivative)."""
+    base = np.asarray(eps_field, dtype=np.float64)
+    d_eps = []
+    for (x, y) in cells:
+        e = base.astype(np.complex128)
+        e[y, x] += 1j * h
+        d_eps.append(complex_step_nusselt(p, steps, e, T=T, ux=ux, uy=uy).imag / h)
+    d_t = {}
+    for side in sides:
+        im = [0.0, 0.0, 0.0, 0.0]
+        im[SIDE[side]] = h
+        d_t[side] = complex_step_nusselt(p, steps, base, tuple(im), T=T, ux=ux, uy=uy).imag / h
+    return np.array(d_eps), d_t
 
 
 def _nan_or(v):

@@ -55,6 +55,22 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* The same source builds twice: with real_t = double (the oracle), and with
+ * real_t = double complex (-DORC_COMPLEX) for complex-step derivatives: a
+ * tiny imaginary perturbation h of one input gives d(output)/d(input) as
+ * Im(output)/h to machine precision, with no subtraction.  Comparisons and
+ * pivot choices look at real parts only. */
+#ifdef ORC_COMPLEX
+#include <complex.h>
+typedef double complex real_t;
+#define RSQRT(x) csqrt(x)
+#define RE(x) creal(x)
+#else
+typedef double real_t;
+#define RSQRT(x) sqrt(x)
+#define RE(x) (x)
+#endif
+
 /* ------------------------------------------------------------------ lattice */
 
 static int CX[9], CY[9];
@@ -120,41 +136,41 @@ typedef struct {
 
 /* Porosity-dependent constants of one node. */
 typedef struct {
-    double eps, nu_over_K, Feps_over_sqrtK, c0, c1;
+    real_t eps, nu_over_K, Feps_over_sqrtK, c0, c1;
 } orc_cell;
 
 /* Everything a node update needs. */
 typedef struct {
     const orc_problem *pb;
     orc_derived d;
-    const double *eps_field; /* [ny][nx] or NULL */
+    const real_t *eps_field; /* [ny][nx] or NULL */
 } orc_ctx;
 
 /* Moments of one node (or the boundary state of a wall node). */
 typedef struct {
-    double T, u[2], F[2], p, S[2][2], gradT[2];
+    real_t T, u[2], F[2], p, S[2][2], gradT[2];
 } orc_state;
 
-static int is_nan(double v) { return v != v; }
+static int is_nan(real_t v) { return v != v; }
 
 /* Derivation of the lattice constants.  U = Ma c_s is the characteristic
  * velocity of Sec. 4; g beta, nu and alpha_e invert the definitions of Ra and
  * Pr (Sec. 2) with U^2 = g beta dT L; nu_e = J nu; A and B from
  * nu_e = c_s^2 (tau_f - A - 1/2) and alpha_e = sigma c_s^2 (tau_T - B - 1/2)
  * (Appendix A and Eq. Therdiff), which for J = 1 is exactly Eq. (EQA&B);
- * K = Da L^2 (Sec. 2); F_eps = 1.75 / sqrt(150 eps^3) (Ergun). */
+ * K = Da L^2 (Sec. 2); F_eps = 1.75 / RSQRT(150 eps^3) (Ergun). */
 int orc_derive(const orc_problem *pb, orc_derived *d) {
     lattice_init();
     memset(d, 0, sizeof(*d));
-    d->L = is_nan(pb->L) ? (double)(pb->nx - 1) : pb->L;
+    d->L = is_nan(pb->L) ? (real_t)(pb->nx - 1) : pb->L;
     d->T0 = 0.5 * (pb->Th + pb->Tc);
     d->dT = pb->Th - pb->Tc;
-    d->U = pb->Ma * sqrt(CS2);
+    d->U = pb->Ma * RSQRT(CS2);
     if (!is_nan(pb->gbeta)) d->gbeta = pb->gbeta;
     else d->gbeta = d->U * d->U / (d->dT * d->L);
     if (!is_nan(pb->nu)) d->nu = pb->nu;
     else if (!is_nan(pb->A)) d->nu = CS2 * (pb->tau_f - pb->A - 0.5) / pb->J;
-    else d->nu = d->U * d->L * sqrt(pb->Pr / pb->Ra);
+    else d->nu = d->U * d->L * RSQRT(pb->Pr / pb->Ra);
     d->nu_e = pb->J * d->nu;
     if (!is_nan(pb->alpha_e)) d->alpha_e = pb->alpha_e;
     else if (!is_nan(pb->B)) d->alpha_e = pb->sigma * CS2 * (pb->tau_T - pb->B - 0.5);
@@ -163,7 +179,7 @@ int orc_derive(const orc_problem *pb, orc_derived *d) {
     d->B = is_nan(pb->B) ? pb->tau_T - 0.5 - d->alpha_e / (pb->sigma * CS2) : pb->B;
     if (pb->da_infinite) d->K = INFINITY;
     else d->K = is_nan(pb->K) ? pb->Da * d->L * d->L : pb->K;
-    d->Feps = pb->forchheimer ? 1.75 / sqrt(150.0 * pb->eps * pb->eps * pb->eps) : 0.0;
+    d->Feps = pb->forchheimer ? 1.75 / RSQRT(150.0 * pb->eps * pb->eps * pb->eps) : 0.0;
     d->kappa_f = 1.0 - 1.0 / (2.0 * pb->tau_f);
     d->kappa_T = 1.0 - 1.0 / (2.0 * pb->tau_T);
     /* admissibility (Sec. 4): 0 < eps <= 1, tau > 1/2, A < tau_f - 1/2,
@@ -184,60 +200,60 @@ int orc_derive(const orc_problem *pb, orc_derived *d) {
 /* K and F_eps at porosity eps.  A porosity field scales K with the
  * Kozeny-Carman form of the Ergun permeability, K ~ eps^3 / (1 - eps)^2
  * (Sec. 2), anchored at K(eps_ref) = Da L^2 with eps_ref the scalar eps. */
-static void cell_constants(const orc_ctx *cx, double eps, orc_cell *c) {
+static void cell_constants(const orc_ctx *cx, real_t eps, orc_cell *c) {
     const orc_problem *pb = cx->pb;
-    double K = cx->d.K, Feps = cx->d.Feps;
+    real_t K = cx->d.K, Feps = cx->d.Feps;
     if (cx->eps_field && !pb->da_infinite) {
-        double er = pb->eps;
-        double kc = (eps * eps * eps / ((1.0 - eps) * (1.0 - eps)))
+        real_t er = pb->eps;
+        real_t kc = (eps * eps * eps / ((1.0 - eps) * (1.0 - eps)))
                   / (er * er * er / ((1.0 - er) * (1.0 - er)));
         K = cx->d.K * kc;
-        Feps = pb->forchheimer ? 1.75 / sqrt(150.0 * eps * eps * eps) : 0.0;
+        Feps = pb->forchheimer ? 1.75 / RSQRT(150.0 * eps * eps * eps) : 0.0;
     }
     c->eps = eps;
-    c->nu_over_K = isinf(K) ? 0.0 : cx->d.nu / K;
-    c->Feps_over_sqrtK = isinf(K) ? 0.0 : Feps / sqrt(K);
+    c->nu_over_K = isinf(RE(K)) ? 0.0 : cx->d.nu / K;
+    c->Feps_over_sqrtK = isinf(RE(K)) ? 0.0 : Feps / RSQRT(K);
     c->c0 = 0.5 * (1.0 + eps * 0.5 * c->nu_over_K);
     c->c1 = eps * 0.5 * c->Feps_over_sqrtK;
 }
 
-static double node_eps(const orc_ctx *cx, int x, int y) {
+static real_t node_eps(const orc_ctx *cx, int x, int y) {
     return cx->eps_field ? cx->eps_field[(size_t)y * cx->pb->nx + x] : cx->pb->eps;
 }
 
 /* ------------------------------------------------ per-direction functions */
 
 /* X : (c_i c_i - c_s^2 I) for a 2x2 tensor X, index by index. */
-static double contract_ccI(int i, double X[2][2]) {
+static real_t contract_ccI(int i, real_t X[2][2]) {
     double c[2] = {(double)CX[i], (double)CY[i]};
-    double s = 0.0;
+    real_t s = 0.0;
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             s += X[a][b] * (c[a] * c[b] - CS2 * (a == b ? 1.0 : 0.0));
     return s;
 }
 
-static double dot_c(int i, const double v[2]) { return CX[i] * v[0] + CY[i] * v[1]; }
+static real_t dot_c(int i, const real_t v[2]) { return CX[i] * v[0] + CY[i] * v[1]; }
 
 /* s_i(u) of Eq. (EQTSHIN). */
-static double s_i(int i, const double u[2], double eps) {
-    double uu[2][2];
+static real_t s_i(int i, const real_t u[2], real_t eps) {
+    real_t uu[2][2];
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) uu[a][b] = u[a] * u[b];
     return WGT[i] * (dot_c(i, u) / CS2 + contract_ccI(i, uu) / (2.0 * eps * CS2 * CS2));
 }
 
 /* r_i of Eq. (EQTSHIN) (dt = 1). */
-static double r_i(int i, double A, double S[2][2]) {
+static real_t r_i(int i, real_t A, real_t S[2][2]) {
     return WGT[i] * A * contract_ccI(i, S) / (2.0 * CS2);
 }
 
 /* Flow EDF, Eq. (EQFIN); with_r = 0 gives f^{e(0)} of Appendix A. */
-static void flow_eq(const orc_ctx *cx, const orc_cell *c, double p, const double u[2],
-                    double S[2][2], int with_r, double out[9]) {
-    double rho0 = cx->pb->rho0, A = cx->d.A, eps = c->eps;
+static void flow_eq(const orc_ctx *cx, const orc_cell *c, real_t p, const real_t u[2],
+                    real_t S[2][2], int with_r, real_t out[9]) {
+    real_t rho0 = cx->pb->rho0, A = cx->d.A, eps = c->eps;
     for (int i = 0; i < 9; ++i) {
-        double r = with_r ? r_i(i, A, S) : 0.0;
+        real_t r = with_r ? r_i(i, A, S) : 0.0;
         if (i == 0)
             out[i] = rho0 - (1.0 - WGT[0]) * eps * p / CS2 + rho0 * s_i(0, u, eps) + rho0 * r;
         else
@@ -246,10 +262,10 @@ static void flow_eq(const orc_ctx *cx, const orc_cell *c, double p, const double
 }
 
 /* Forcing term F_i, Eq. (FtermF). */
-static void flow_force_terms(const orc_ctx *cx, const orc_cell *c, const double u[2],
-                             const double F[2], double out[9]) {
-    double rho0 = cx->pb->rho0, eps = c->eps, kf = cx->d.kappa_f;
-    double uFFu[2][2];
+static void flow_force_terms(const orc_ctx *cx, const orc_cell *c, const real_t u[2],
+                             const real_t F[2], real_t out[9]) {
+    real_t rho0 = cx->pb->rho0, eps = c->eps, kf = cx->d.kappa_f;
+    real_t uFFu[2][2];
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) uFFu[a][b] = u[a] * F[b] + F[a] * u[b];
     for (int i = 0; i < 9; ++i)
@@ -258,14 +274,14 @@ static void flow_force_terms(const orc_ctx *cx, const orc_cell *c, const double 
 }
 
 /* Temperature EDF, Eq. (TeEDFEQ); with_grad = 0 gives g^{e(0)} of Sec. 3.2. */
-static void thermal_eq(const orc_ctx *cx, const orc_cell *c, double T, const double u[2],
-                       double p, const double gradT[2], int with_grad, double out[9]) {
-    double sigma = cx->pb->sigma, rho0 = cx->pb->rho0, eps = c->eps, B = cx->d.B;
-    double uu[2][2];
+static void thermal_eq(const orc_ctx *cx, const orc_cell *c, real_t T, const real_t u[2],
+                       real_t p, const real_t gradT[2], int with_grad, real_t out[9]) {
+    real_t sigma = cx->pb->sigma, rho0 = cx->pb->rho0, eps = c->eps, B = cx->d.B;
+    real_t uu[2][2];
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) uu[a][b] = u[a] * u[b];
     for (int i = 0; i < 9; ++i) {
-        double v = WGT[i] * T *
+        real_t v = WGT[i] * T *
                        (sigma + dot_c(i, u) / CS2 + contract_ccI(i, uu) / (2.0 * eps * CS2 * CS2)) +
                    VARPI[i] * T * eps * p / (CS2 * rho0);
         if (with_grad) v += sigma * WGT[i] * B * dot_c(i, gradT);
@@ -274,14 +290,14 @@ static void thermal_eq(const orc_ctx *cx, const orc_cell *c, double T, const dou
 }
 
 /* Source P_i, Eq. (Eq:Tforce). uu:(c_i gradT) = sum_ab u_a u_b c_a dT/dx_b. */
-static void thermal_P(const orc_ctx *cx, const orc_cell *c, double T, const double u[2],
-                      double p, const double F[2], const double gradT[2], double out[9]) {
-    double sigma = cx->pb->sigma, rho0 = cx->pb->rho0, eps = c->eps, kT = cx->d.kappa_T;
-    double w[2];
+static void thermal_P(const orc_ctx *cx, const orc_cell *c, real_t T, const real_t u[2],
+                      real_t p, const real_t F[2], const real_t gradT[2], real_t out[9]) {
+    real_t sigma = cx->pb->sigma, rho0 = cx->pb->rho0, eps = c->eps, kT = cx->d.kappa_T;
+    real_t w[2];
     for (int a = 0; a < 2; ++a) w[a] = T * F[a] + eps * p * gradT[a] / rho0;
     for (int i = 0; i < 9; ++i) {
         double ci[2] = {(double)CX[i], (double)CY[i]};
-        double uuc = 0.0;
+        real_t uuc = 0.0;
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) uuc += u[a] * u[b] * ci[a] * gradT[b];
         out[i] = WGT[i] * kT * (dot_c(i, w) / CS2 + (1.0 / eps - 1.0 / sigma) * uuc / CS2);
@@ -289,40 +305,40 @@ static void thermal_P(const orc_ctx *cx, const orc_cell *c, double T, const doub
 }
 
 /* Source Q_i of Sec. 3.2. */
-static void thermal_Q(const orc_ctx *cx, const double u[2], double out[9]) {
-    double sigma = cx->pb->sigma, kT = cx->d.kappa_T, Q = cx->pb->Q;
+static void thermal_Q(const orc_ctx *cx, const real_t u[2], real_t out[9]) {
+    real_t sigma = cx->pb->sigma, kT = cx->d.kappa_T, Q = cx->pb->Q;
     for (int i = 0; i < 9; ++i) out[i] = WGT[i] * kT * (1.0 + dot_c(i, u) / (sigma * CS2)) * Q;
 }
 
 /* Total force, Eq. (ForceEq), with G = g beta (T - T0) j + a. */
-static void total_force(const orc_ctx *cx, const orc_cell *c, double T, const double u[2],
-                        double F[2]) {
-    double G[2] = {cx->pb->ax, cx->d.gbeta * (T - cx->d.T0) + cx->pb->ay};
-    double umag = sqrt(u[0] * u[0] + u[1] * u[1]);
+static void total_force(const orc_ctx *cx, const orc_cell *c, real_t T, const real_t u[2],
+                        real_t F[2]) {
+    real_t G[2] = {cx->pb->ax, cx->d.gbeta * (T - cx->d.T0) + cx->pb->ay};
+    real_t umag = RSQRT(u[0] * u[0] + u[1] * u[1]);
     for (int a = 0; a < 2; ++a)
         F[a] = -c->eps * c->nu_over_K * u[a] - c->eps * c->Feps_over_sqrtK * umag * u[a] +
                c->eps * G[a];
 }
 
 /* Velocity from the temporary velocity v (Sec. 3.1). */
-static void velocity_from_v(const orc_cell *c, const double v[2], double u[2]) {
-    double vmag = sqrt(v[0] * v[0] + v[1] * v[1]);
-    double den = c->c0 + sqrt(c->c0 * c->c0 + c->c1 * vmag);
+static void velocity_from_v(const orc_cell *c, const real_t v[2], real_t u[2]) {
+    real_t vmag = RSQRT(v[0] * v[0] + v[1] * v[1]);
+    real_t den = c->c0 + RSQRT(c->c0 * c->c0 + c->c1 * vmag);
     u[0] = v[0] / den;
     u[1] = v[1] / den;
 }
 
 /* Solve the 2x2 system M x = N by Gaussian elimination with partial
  * pivoting.  Returns 0, or 1 when M is singular. */
-static int solve2(double M[2][2], const double N[2], double x[2]) {
-    double a[2][3] = {{M[0][0], M[0][1], N[0]}, {M[1][0], M[1][1], N[1]}};
-    if (fabs(a[1][0]) > fabs(a[0][0])) {
-        for (int k = 0; k < 3; ++k) { double t = a[0][k]; a[0][k] = a[1][k]; a[1][k] = t; }
+static int solve2(real_t M[2][2], const real_t N[2], real_t x[2]) {
+    real_t a[2][3] = {{M[0][0], M[0][1], N[0]}, {M[1][0], M[1][1], N[1]}};
+    if (fabs(RE(a[1][0])) > fabs(RE(a[0][0]))) {
+        for (int k = 0; k < 3; ++k) { real_t t = a[0][k]; a[0][k] = a[1][k]; a[1][k] = t; }
     }
-    if (a[0][0] == 0.0) return 1;
-    double m = a[1][0] / a[0][0];
+    if (RE(a[0][0]) == 0.0) return 1;
+    real_t m = a[1][0] / a[0][0];
     for (int k = 0; k < 3; ++k) a[1][k] -= m * a[0][k];
-    if (a[1][1] == 0.0) return 1;
+    if (RE(a[1][1]) == 0.0) return 1;
     x[1] = a[1][2] / a[1][1];
     x[0] = (a[0][2] - a[0][1] * x[1]) / a[0][0];
     return 0;
@@ -330,47 +346,47 @@ static int solve2(double M[2][2], const double N[2], double x[2]) {
 
 /* Moments of one node from its post-streaming populations (Sec. 3.1-3.3):
  * T first (this step's g), then buoyancy, v, u, F, p, S, grad T. */
-static void node_moments(const orc_ctx *cx, const orc_cell *c, const double fs[9],
-                         const double gs[9], orc_state *m) {
+static void node_moments(const orc_ctx *cx, const orc_cell *c, const real_t fs[9],
+                         const real_t gs[9], orc_state *m) {
     const orc_problem *pb = cx->pb;
-    double rho0 = pb->rho0, eps = c->eps, sigma = pb->sigma;
+    real_t rho0 = pb->rho0, eps = c->eps, sigma = pb->sigma;
     /* sigma T = sum_i g_i + (dt/2) Q */
-    double sg = 0.0;
+    real_t sg = 0.0;
     for (int i = 0; i < 9; ++i) sg += gs[i];
     m->T = (sg + 0.5 * pb->Q) / sigma;
     /* v = sum_i c_i f_i / rho0 + (dt/2) eps G */
-    double G[2] = {pb->ax, cx->d.gbeta * (m->T - cx->d.T0) + pb->ay};
-    double v[2] = {0.0, 0.0};
+    real_t G[2] = {pb->ax, cx->d.gbeta * (m->T - cx->d.T0) + pb->ay};
+    real_t v[2] = {0.0, 0.0};
     for (int i = 0; i < 9; ++i) { v[0] += CX[i] * fs[i]; v[1] += CY[i] * fs[i]; }
     for (int a = 0; a < 2; ++a) v[a] = v[a] / rho0 + 0.5 * eps * G[a];
     velocity_from_v(c, v, m->u);
     total_force(cx, c, m->T, m->u, m->F);
     /* p = c_s^2 / (eps (1 - w_0)) [sum_{i!=0} f_i + tau_f dt F_0 + rho0 s_0(u)] */
-    double Fi[9];
+    real_t Fi[9];
     flow_force_terms(cx, c, m->u, m->F, Fi);
-    double sf = 0.0;
+    real_t sf = 0.0;
     for (int i = 1; i < 9; ++i) sf += fs[i];
     m->p = CS2 / (eps * (1.0 - WGT[0])) * (sf + pb->tau_f * Fi[0] + rho0 * s_i(0, m->u, eps));
     /* S, Eq. (ShearEqCom) */
-    double fe0[9], zero[2][2] = {{0, 0}, {0, 0}};
+    real_t fe0[9], zero[2][2] = {{0, 0}, {0, 0}};
     flow_eq(cx, c, m->p, m->u, zero, 0, fe0);
-    double Pi[2][2] = {{0, 0}, {0, 0}};
+    real_t Pi[2][2] = {{0, 0}, {0, 0}};
     for (int i = 0; i < 9; ++i) {
         double ci[2] = {(double)CX[i], (double)CY[i]};
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) Pi[a][b] += ci[a] * ci[b] * (fs[i] - fe0[i]);
     }
-    double den = CS2 * rho0 * (cx->d.A - pb->tau_f);
+    real_t den = CS2 * rho0 * (cx->d.A - pb->tau_f);
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             m->S[a][b] = (Pi[a][b] + 0.5 * rho0 * (m->u[a] * m->F[b] + m->F[a] * m->u[b]) / eps) / den;
     /* grad T, Eqs. (TeEqCom)-(MatrN) */
-    double ge0[9], g0[2] = {0.0, 0.0};
+    real_t ge0[9], g0[2] = {0.0, 0.0};
     thermal_eq(cx, c, m->T, m->u, m->p, g0, 0, ge0);
-    double N[2] = {0.0, 0.0};
+    real_t N[2] = {0.0, 0.0};
     for (int i = 0; i < 9; ++i) { N[0] += CX[i] * (gs[i] - ge0[i]); N[1] += CY[i] * (gs[i] - ge0[i]); }
     for (int a = 0; a < 2; ++a) N[a] += 0.5 * (m->T * m->F[a] + m->u[a] * pb->Q / sigma);
-    double M[2][2];
+    real_t M[2][2];
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             M[a][b] = (-eps * m->p / (2.0 * rho0) + CS2 * sigma * (cx->d.B - pb->tau_T)) * (a == b ? 1.0 : 0.0) -
@@ -384,7 +400,7 @@ static int wrap(int v, int n) { v %= n; return v < 0 ? v + n : v; }
 
 /* Post-streaming population i at (x, y): the post-collision value that
  * streamed in from x - c_i (streaming step of Sec. 3.2, pull form). */
-static double pull(const orc_ctx *cx, const double *h, int i, int x, int y) {
+static real_t pull(const orc_ctx *cx, const real_t *h, int i, int x, int y) {
     int nx = cx->pb->nx, ny = cx->pb->ny;
     int xs = wrap(x - CX[i], nx), ys = wrap(y - CY[i], ny);
     return h[((size_t)i * ny + ys) * nx + xs];
@@ -394,10 +410,22 @@ typedef struct {
     int wall;
     int xf, yf, xff, yff;
     int dirichlet;
-    double Tb;
-    double ub[2];
+    real_t Tb;
+    real_t ub[2];
     int fixed_grad[2]; /* wall-normal gradient components prescribed (= 0) */
 } orc_wall;
+
+#ifdef ORC_COMPLEX
+/* Imaginary parts added to the Dirichlet wall temperatures (complex build). */
+static double g_tbc_imag[4];
+int orc_cs_set_tbc_imag(const double im[4]) {
+    for (int k = 0; k < 4; ++k) g_tbc_imag[k] = im[k];
+    return 0;
+}
+static real_t tbc_value(const orc_problem *pb, int side) { return pb->T_bc[side] + I * g_tbc_imag[side]; }
+#else
+static real_t tbc_value(const orc_problem *pb, int side) { return pb->T_bc[side]; }
+#endif
 
 static void classify(const orc_ctx *cx, int x, int y, orc_wall *w) {
     const orc_problem *pb = cx->pb;
@@ -417,7 +445,7 @@ static void classify(const orc_ctx *cx, int x, int y, orc_wall *w) {
     int tside = -1;
     if (xs >= 0 && pb->bc[xs] == ORC_WALL_DIRICHLET) tside = xs;
     else if (ys >= 0 && pb->bc[ys] == ORC_WALL_DIRICHLET) tside = ys;
-    if (tside >= 0) { w->dirichlet = 1; w->Tb = pb->T_bc[tside]; }
+    if (tside >= 0) { w->dirichlet = 1; w->Tb = tbc_value(pb, tside); }
     else {
         w->dirichlet = 0;
         w->fixed_grad[0] = (xs >= 0);
@@ -433,14 +461,14 @@ static void classify(const orc_ctx *cx, int x, int y, orc_wall *w) {
  * S(x_f), grad T_b, F at (u_b, T_b).  When rebuilt is non-NULL the wall
  * node's rebuilt post-streaming populations (Eqs. NEESVel, TNEESAp) are
  * written there; for interior nodes the pulled populations are. */
-static void node_state(const orc_ctx *cx, const double *f, const double *g, int x, int y,
-                       orc_state *st, double fr[9], double gr[9]) {
+static void node_state(const orc_ctx *cx, const real_t *f, const real_t *g, int x, int y,
+                       orc_state *st, real_t fr[9], real_t gr[9]) {
     orc_wall w;
     classify(cx, x, y, &w);
     orc_cell c;
     cell_constants(cx, node_eps(cx, x, y), &c);
     if (!w.wall) {
-        double fs[9], gs[9];
+        real_t fs[9], gs[9];
         for (int i = 0; i < 9; ++i) { fs[i] = pull(cx, f, i, x, y); gs[i] = pull(cx, g, i, x, y); }
         node_moments(cx, &c, fs, gs, st);
         if (fr) for (int i = 0; i < 9; ++i) { fr[i] = fs[i]; gr[i] = gs[i]; }
@@ -449,7 +477,7 @@ static void node_state(const orc_ctx *cx, const double *f, const double *g, int 
     /* state at x_f from its own post-streaming populations */
     orc_cell cf;
     cell_constants(cx, node_eps(cx, w.xf, w.yf), &cf);
-    double ff[9], gf[9];
+    real_t ff[9], gf[9];
     for (int i = 0; i < 9; ++i) { ff[i] = pull(cx, f, i, w.xf, w.yf); gf[i] = pull(cx, g, i, w.xf, w.yf); }
     orc_state sf;
     node_moments(cx, &cf, ff, gf, &sf);
@@ -465,13 +493,13 @@ static void node_state(const orc_ctx *cx, const double *f, const double *g, int 
         /* Eq. (TNEESApGra) with a zero prescribed normal gradient */
         orc_cell cff;
         cell_constants(cx, node_eps(cx, w.xff, w.yff), &cff);
-        double fff[9], gff[9];
+        real_t fff[9], gff[9];
         for (int i = 0; i < 9; ++i) { fff[i] = pull(cx, f, i, w.xff, w.yff); gff[i] = pull(cx, g, i, w.xff, w.yff); }
         orc_state sff;
         node_moments(cx, &cff, fff, gff, &sff);
         for (int a = 0; a < 2; ++a)
             if (w.fixed_grad[a]) st->gradT[a] = 0.0;
-        double dl = 0.0; /* Delta . grad T_b, Delta = x_f - x_b */
+        real_t dl = 0.0; /* Delta . grad T_b, Delta = x_f - x_b */
         dl += (w.xf - x) * st->gradT[0] * w.fixed_grad[0];
         dl += (w.yf - y) * st->gradT[1] * w.fixed_grad[1];
         st->T = (4.0 * sf.T - sff.T - 2.0 * dl) / 3.0;
@@ -479,7 +507,7 @@ static void node_state(const orc_ctx *cx, const double *f, const double *g, int 
     total_force(cx, &c, st->T, st->u, st->F);
     if (fr) {
         /* f(x_b) = f^eq(x_b) + [f(x_f) - f^eq(x_f)], Eq. (NEESVel) */
-        double eqb[9], eqf[9];
+        real_t eqb[9], eqf[9];
         flow_eq(cx, &c, st->p, st->u, st->S, 1, eqb);
         flow_eq(cx, &cf, sf.p, sf.u, sf.S, 1, eqf);
         for (int i = 0; i < 9; ++i) fr[i] = eqb[i] + (ff[i] - eqf[i]);
@@ -492,14 +520,14 @@ static void node_state(const orc_ctx *cx, const double *f, const double *g, int 
 
 /* One node of one time step: stream (pull), rebuild walls, collide
  * (Eqs. LBEeq and TEqColli). */
-static void node_update(const orc_ctx *cx, const double *f, const double *g, int x, int y,
-                        double fo[9], double go[9]) {
+static void node_update(const orc_ctx *cx, const real_t *f, const real_t *g, int x, int y,
+                        real_t fo[9], real_t go[9]) {
     orc_state st;
-    double fr[9], gr[9];
+    real_t fr[9], gr[9];
     node_state(cx, f, g, x, y, &st, fr, gr);
     orc_cell c;
     cell_constants(cx, node_eps(cx, x, y), &c);
-    double feq[9], Fi[9], geq[9], Pi[9], Qi[9];
+    real_t feq[9], Fi[9], geq[9], Pi[9], Qi[9];
     flow_eq(cx, &c, st.p, st.u, st.S, 1, feq);
     flow_force_terms(cx, &c, st.u, st.F, Fi);
     thermal_eq(cx, &c, st.T, st.u, st.p, st.gradT, 1, geq);
@@ -512,7 +540,7 @@ static void node_update(const orc_ctx *cx, const double *f, const double *g, int
     }
 }
 
-static int make_ctx(const orc_problem *pb, const double *eps_field, orc_ctx *cx) {
+static int make_ctx(const orc_problem *pb, const real_t *eps_field, orc_ctx *cx) {
     cx->pb = pb;
     cx->eps_field = eps_field;
     return orc_derive(pb, &cx->d);
@@ -520,6 +548,7 @@ static int make_ctx(const orc_problem *pb, const double *eps_field, orc_ctx *cx)
 
 /* ------------------------------------------------------------ public API */
 
+#ifndef ORC_COMPLEX
 int orc_lattice(int32_t cx_out[9], int32_t cy_out[9], double w_out[9], double varpi_out[9]) {
     lattice_init();
     for (int i = 0; i < 9; ++i) { cx_out[i] = CX[i]; cy_out[i] = CY[i]; w_out[i] = WGT[i]; varpi_out[i] = VARPI[i]; }
@@ -591,23 +620,25 @@ int orc_cell_velocity(const orc_problem *pb, double eps, const double v[2], doub
     return 0;
 }
 
+#endif /* !ORC_COMPLEX */
+
 /* Initial post-collision state from macroscopic fields (NULL = uniform):
  * f = f^{eq}(p = 0, u, S = 0), g = g^{eq}(T, u, p = 0, grad T = 0). */
-int orc_init(const orc_problem *pb, const double *T, const double *ux, const double *uy,
-             const double *eps_field, double *f, double *g) {
+int orc_init(const orc_problem *pb, const real_t *T, const real_t *ux, const real_t *uy,
+             const real_t *eps_field, real_t *f, real_t *g) {
     orc_ctx cx;
     int rc = make_ctx(pb, eps_field, &cx);
     if (rc) return rc;
     int nx = pb->nx, ny = pb->ny;
-    double S[2][2] = {{0, 0}, {0, 0}}, z[2] = {0, 0};
+    real_t S[2][2] = {{0, 0}, {0, 0}}, z[2] = {0, 0};
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t k = (size_t)y * nx + x;
             orc_cell c;
             cell_constants(&cx, node_eps(&cx, x, y), &c);
-            double u[2] = {ux ? ux[k] : 0.0, uy ? uy[k] : 0.0};
-            double t = T ? T[k] : pb->T_init;
-            double fe[9], ge[9];
+            real_t u[2] = {ux ? ux[k] : 0.0, uy ? uy[k] : 0.0};
+            real_t t = T ? T[k] : pb->T_init;
+            real_t fe[9], ge[9];
             flow_eq(&cx, &c, 0.0, u, S, 1, fe);
             thermal_eq(&cx, &c, t, u, 0.0, z, 1, ge);
             for (int i = 0; i < 9; ++i) {
@@ -620,29 +651,29 @@ int orc_init(const orc_problem *pb, const double *T, const double *ux, const dou
 
 /* n time steps; f and g are updated in place (the oracle ping-pongs through
  * a private copy). */
-int orc_run(const orc_problem *pb, const double *eps_field, double *f, double *g, int64_t n) {
+int orc_run(const orc_problem *pb, const real_t *eps_field, real_t *f, real_t *g, int64_t n) {
     orc_ctx cx;
     int rc = make_ctx(pb, eps_field, &cx);
     if (rc) return rc;
     int nx = pb->nx, ny = pb->ny;
     size_t plane = (size_t)nx * ny, tot = 9 * plane;
-    double *f2 = (double *)malloc(tot * sizeof(double));
-    double *g2 = (double *)malloc(tot * sizeof(double));
+    real_t *f2 = (real_t *)malloc(tot * sizeof(real_t));
+    real_t *g2 = (real_t *)malloc(tot * sizeof(real_t));
     if (!f2 || !g2) { free(f2); free(g2); return 100; }
-    double *fa = f, *ga = g, *fb = f2, *gb = g2;
+    real_t *fa = f, *ga = g, *fb = f2, *gb = g2;
     for (int64_t s = 0; s < n; ++s) {
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
-                double fo[9], go[9];
+                real_t fo[9], go[9];
                 node_update(&cx, fa, ga, x, y, fo, go);
                 size_t k = (size_t)y * nx + x;
                 for (int i = 0; i < 9; ++i) { fb[i * plane + k] = fo[i]; gb[i * plane + k] = go[i]; }
             }
-        double *t;
+        real_t *t;
         t = fa; fa = fb; fb = t;
         t = ga; ga = gb; gb = t;
     }
-    if (fa != f) { memcpy(f, fa, tot * sizeof(double)); memcpy(g, ga, tot * sizeof(double)); }
+    if (fa != f) { memcpy(f, fa, tot * sizeof(real_t)); memcpy(g, ga, tot * sizeof(real_t)); }
     free(f2);
     free(g2);
     return 0;
@@ -650,9 +681,9 @@ int orc_run(const orc_problem *pb, const double *eps_field, double *f, double *g
 
 /* One step evaluated only at the listed nodes: fo/go[k][9] are the new
  * post-collision populations of node (xs[k], ys[k]). */
-int orc_update_nodes(const orc_problem *pb, const double *eps_field, const double *f,
-                     const double *g, int64_t n, const int32_t *xs, const int32_t *ys,
-                     double *fo, double *go) {
+int orc_update_nodes(const orc_problem *pb, const real_t *eps_field, const real_t *f,
+                     const real_t *g, int64_t n, const int32_t *xs, const int32_t *ys,
+                     real_t *fo, real_t *go) {
     orc_ctx cx;
     int rc = make_ctx(pb, eps_field, &cx);
     if (rc) return rc;
@@ -662,8 +693,8 @@ int orc_update_nodes(const orc_problem *pb, const double *eps_field, const doubl
 
 /* Macroscopic fields of the state: the moments a next step would compute
  * after streaming (wall nodes: the NEES boundary state). */
-int orc_moments(const orc_problem *pb, const double *eps_field, const double *f, const double *g,
-                double *p, double *ux, double *uy, double *T) {
+int orc_moments(const orc_problem *pb, const real_t *eps_field, const real_t *f, const real_t *g,
+                real_t *p, real_t *ux, real_t *uy, real_t *T) {
     orc_ctx cx;
     int rc = make_ctx(pb, eps_field, &cx);
     if (rc) return rc;
@@ -682,9 +713,9 @@ int orc_moments(const orc_problem *pb, const double *eps_field, const double *f,
 }
 
 /* Shear rate and temperature gradient fields (local schemes). */
-int orc_gradients(const orc_problem *pb, const double *eps_field, const double *f,
-                  const double *g, double *Sxx, double *Sxy, double *Syy, double *dTdx,
-                  double *dTdy) {
+int orc_gradients(const orc_problem *pb, const real_t *eps_field, const real_t *f,
+                  const real_t *g, real_t *Sxx, real_t *Sxy, real_t *Syy, real_t *dTdx,
+                  real_t *dTdy) {
     orc_ctx cx;
     int rc = make_ctx(pb, eps_field, &cx);
     if (rc) return rc;
@@ -705,41 +736,42 @@ int orc_gradients(const orc_problem *pb, const double *eps_field, const double *
  * into the wall by the second-order one-sided difference; the mean is the
  * trapezoid rule over the wall's nodes divided by its length in lattice
  * units.  nu_local has ny entries (W, E) or nx entries (S, N). */
-int orc_nusselt(const orc_problem *pb, const double *T, int side, double *nu_local,
-                double *nu_mean) {
+int orc_nusselt(const orc_problem *pb, const real_t *T, int side, real_t *nu_local,
+                real_t *nu_mean) {
     orc_derived d;
     int rc = orc_derive(pb, &d);
     if (rc) return rc;
     int nx = pb->nx, ny = pb->ny;
     int n = (side <= SIDE_E) ? ny : nx;
-    double acc = 0.0;
+    real_t acc = 0.0;
     for (int j = 0; j < n; ++j) {
-        double t0, t1, t2;
+        real_t t0, t1, t2;
         if (side == SIDE_W) { t0 = T[(size_t)j * nx + 0]; t1 = T[(size_t)j * nx + 1]; t2 = T[(size_t)j * nx + 2]; }
         else if (side == SIDE_E) { t0 = T[(size_t)j * nx + nx - 1]; t1 = T[(size_t)j * nx + nx - 2]; t2 = T[(size_t)j * nx + nx - 3]; }
         else if (side == SIDE_S) { t0 = T[j]; t1 = T[(size_t)nx + j]; t2 = T[(size_t)2 * nx + j]; }
         else { t0 = T[(size_t)(ny - 1) * nx + j]; t1 = T[(size_t)(ny - 2) * nx + j]; t2 = T[(size_t)(ny - 3) * nx + j]; }
         /* one-sided second-order derivative taken from the wall inward, then
          * turned into the derivative along +x (W, E) or +y (S, N) */
-        double d_in = (-3.0 * t0 + 4.0 * t1 - t2) / 2.0;
-        double d_axis = (side == SIDE_W || side == SIDE_S) ? d_in : -d_in;
-        double nu = -d.L * d_axis / d.dT;
+        real_t d_in = (-3.0 * t0 + 4.0 * t1 - t2) / 2.0;
+        real_t d_axis = (side == SIDE_W || side == SIDE_S) ? d_in : -d_in;
+        real_t nu = -d.L * d_axis / d.dT;
         if (nu_local) nu_local[j] = nu;
-        double wt = (j == 0 || j == n - 1) ? 0.5 : 1.0;
+        real_t wt = (j == 0 || j == n - 1) ? 0.5 : 1.0;
         acc += wt * nu;
     }
-    *nu_mean = acc / (double)(n - 1);
+    *nu_mean = acc / (real_t)(n - 1);
     return 0;
 }
 
+#ifndef ORC_COMPLEX
 /* Steady-state criterion of Sec. 4: res_u = sum |u - u_old|_2 / sum |u|_2,
  * res_T = sum |T - T_old| / sum |T|. */
 int orc_residual(int64_t n, const double *ux, const double *uy, const double *T,
                  const double *ux0, const double *uy0, const double *T0, double out[2]) {
     double nu_ = 0, du = 0, nT = 0, dT = 0;
     for (int64_t k = 0; k < n; ++k) {
-        du += sqrt((ux[k] - ux0[k]) * (ux[k] - ux0[k]) + (uy[k] - uy0[k]) * (uy[k] - uy0[k]));
-        nu_ += sqrt(ux[k] * ux[k] + uy[k] * uy[k]);
+        du += RSQRT((ux[k] - ux0[k]) * (ux[k] - ux0[k]) + (uy[k] - uy0[k]) * (uy[k] - uy0[k]));
+        nu_ += RSQRT(ux[k] * ux[k] + uy[k] * uy[k]);
         dT += fabs(T[k] - T0[k]);
         nT += fabs(T[k]);
     }
@@ -748,10 +780,12 @@ int orc_residual(int64_t n, const double *ux, const double *uy, const double *T,
     return 0;
 }
 
+#endif /* !ORC_COMPLEX */
+
 /* Totals of the post-collision state: out = [sum f (all nine), sum g]. */
-int orc_totals(const orc_problem *pb, const double *f, const double *g, double out[2]) {
+int orc_totals(const orc_problem *pb, const real_t *f, const real_t *g, real_t out[2]) {
     size_t tot = (size_t)9 * pb->nx * pb->ny;
-    double sf = 0, sg = 0;
+    real_t sf = 0, sg = 0;
     for (size_t k = 0; k < tot; ++k) { sf += f[k]; sg += g[k]; }
     out[0] = sf;
     out[1] = sg;
