@@ -134,8 +134,13 @@ const char* lbm_last_error(const lbm_handle* h);
 /* Initialise the state from macroscopic fields: the post-collision
  * populations become f = f^eq(p = 0, u, S = 0) and
  * g = g^eq(T, u, p = 0, grad T = 0) (Eqs. EQFIN, TeEDFEQ).  Any of T, ux, uy
- * may be NULL (T_init, 0, 0).  eps_field must be NULL (a uniform porosity
- * eps is used).  Resets the step counter and the non-finite flag. */
+ * may be NULL (T_init, 0, 0).  eps_field: a porosity field [ny][nx] with
+ * values in (0, 1), or NULL for the uniform porosity eps.  With a field, the
+ * permeability of each node follows the Kozeny-Carman form of the Ergun
+ * relation (Sec. 2), K(e) = Da L^2 [e^3/(1-e)^2] / [eps^3/(1-eps)^2] with
+ * the problem's eps as the reference (which must then be below 1), and
+ * F_eps(e) = 1.75/sqrt(150 e^3).  Resets the step counter and the non-finite
+ * flag. */
 lbm_status lbm_set_fields(lbm_handle* h, const double* T, const double* ux,
                           const double* uy, const double* eps_field,
                           int on_device);
@@ -195,6 +200,26 @@ lbm_status lbm_get_state(lbm_handle* h, double* f, double* g, int on_device);
 /* Load post-collision populations (layout of lbm_get_state; f_0 ignored).
  * Resets the non-finite flag; keeps the step counter. */
 lbm_status lbm_set_state(lbm_handle* h, const double* f, const double* g, int on_device);
+
+/* Discrete adjoint of the hot-wall heat transfer.  From the current state,
+ * advance n_steps steps (the handle ends at step n_steps), evaluate
+ * loss = mean Nusselt number on `side` (as lbm_nusselt, with Th - Tc held at
+ * its nominal value), then run the adjoint of every step backwards and return
+ *   dloss_deps[ny][nx]  d loss / d eps at every node (host; NULL allowed;
+ *                       needs a porosity field set by lbm_set_fields),
+ *   dloss_dTbc[4]       d loss / d (Dirichlet wall temperature) per side
+ *                       W, E, S, N (host; NULL allowed).
+ * States are recomputed from checkpoints kept every `segment` steps
+ * (0 = ceil(sqrt(n_steps))): memory for about 2 sqrt(n_steps) states is
+ * allocated on the handle's stream for the duration of the call and freed
+ * before it returns.  FP64 or FP32 storage; the adjoint arithmetic is that of
+ * the storage type, the gradients are accumulated in FP64.  The derivatives
+ * are those of the discrete step itself (each node's transposed Jacobian is
+ * applied exactly, with the transpose of the streaming), not of the
+ * continuous equations.  The paper has no adjoint; the loss and the
+ * parameters are those of its cavity problem (Sec. 4.2).  Synchronises. */
+lbm_status lbm_adjoint(lbm_handle* h, int64_t n_steps, int64_t segment, int side, double* loss,
+                       double* dloss_deps, double* dloss_dTbc);
 
 /* Steps completed since the last lbm_set_fields. */
 int64_t lbm_steps_done(const lbm_handle* h);

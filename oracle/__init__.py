@@ -143,22 +143,23 @@ def complex_step_nusselt(p: dict, steps: int, eps_field=None, tbc_imag=(0.0, 0.0
 
 
 def nusselt_gradient(p: dict, steps: int, eps_field, cells, sides=("W", "E"), h: float = 1e-30,
-                     T=None, ux=None, uy=None):
-    """Exact discrete derivatives of the hot-wall mean Nusselt number after
-    `steps` steps with respect to eps at each (x, y) in `cells` and to the
-    Dirichlet temperature of each side in `sides`, by the complex-step
+                     T=None, ux=None, uy=None, loss_side: str = "W"):
+    """Exact discrete derivatives of the mean Nusselt number on `loss_side`
+    after `steps` steps with respect to eps at each (x, y) in `cells` and to
+    the Dirichlet temperature of each side in `sides`, by the complex-step
     method (one complex run per derivative)."""
     base = np.asarray(eps_field, dtype=np.float64)
     d_eps = []
     for (x, y) in cells:
         e = base.astype(np.complex128)
         e[y, x] += 1j * h
-        d_eps.append(complex_step_nusselt(p, steps, e, T=T, ux=ux, uy=uy).imag / h)
+        d_eps.append(complex_step_nusselt(p, steps, e, T=T, ux=ux, uy=uy, side=loss_side).imag / h)
     d_t = {}
     for side in sides:
         im = [0.0, 0.0, 0.0, 0.0]
         im[SIDE[side]] = h
-        d_t[side] = complex_step_nusselt(p, steps, base, tuple(im), T=T, ux=ux, uy=uy).imag / h
+        d_t[side] = complex_step_nusselt(p, steps, base, tuple(im), T=T, ux=ux, uy=uy,
+                                         side=loss_side).imag / h
     return np.array(d_eps), d_t
 
 

@@ -13,6 +13,7 @@
 #include <string>
 
 #include "../../include/lbm.h"
+#include "lbm_handle.h"
 #include "lbm_host.h"
 #include "lbm_internal.h"
 
@@ -24,30 +25,6 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
-struct lbm_handle {
-    lbm_params prm;
-    Derived d;
-    Layout L;
-    cudaStream_t stream;
-    char* ws;
-    bool owns_ws;
-    int cur;
-    int64_t steps, launches;
-    bool nonfinite;
-    lbm::KConst<double> k64;
-    lbm::KConst<float> k32;
-    lbm::DiagConst diag;
-    std::string err;
-
-    void* buf(int i) const { return ws + L.off_buf[i]; }
-    double* fields() const { return (double*)(ws + L.off_fields); }
-    double* snap() const { return (double*)(ws + L.off_snap); }
-    double* nu() const { return (double*)(ws + L.off_nu); }
-    double* partial() const { return (double*)(ws + L.off_partial); }
-    double* out() const { return (double*)(ws + L.off_out); }
-    int* flag() const { return (int*)(ws + L.off_flag); }
-    size_t N() const { return (size_t)prm.nx * prm.ny; }
-};
 
 namespace {
 
@@ -56,6 +33,12 @@ lbm_status fail(lbm_handle* h, lbm_status s, const std::string& m) {
     else g_create_error = m;
     return s;
 }
+
+}  // namespace
+
+lbm_status lbm_handle_fail(lbm_handle* h, lbm_status s, const std::string& m) { return fail(h, s, m); }
+
+namespace {
 
 lbm_status cuda_fail(lbm_handle* h, cudaError_t e, const char* what) {
     return fail(h, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -200,9 +183,28 @@ const char* lbm_last_error(const lbm_handle* h) {
 lbm_status lbm_set_fields(lbm_handle* h, const double* T, const double* ux, const double* uy,
                           const double* eps_field, int on_device) {
     if (!h) return LBM_ERR_ARG;
-    if (eps_field) return fail(h, LBM_ERR_ARG, "a porosity field is not supported by this entry point");
     double* F = h->fields();
     const size_t N = h->N();
+    if (eps_field) {
+        if (!(h->prm.eps < 1.0))
+            return fail(h, LBM_ERR_PARAM_RANGE, "a porosity field needs a reference eps below 1");
+        if (!on_device)
+            for (size_t i = 0; i < N; ++i)
+                if (!(eps_field[i] > 0.0 && eps_field[i] < 1.0))
+                    return fail(h, LBM_ERR_PARAM_RANGE, "porosity field values must lie in (0, 1)");
+        lbm_status s0 = copy_in(h, F + 3 * N, eps_field, on_device);
+        if (s0 != LBM_OK) return s0;
+        char* area = h->ws + h->L.off_eps;
+        cudaError_t e = h->prm.precision == LBM_F64
+                            ? lbm::launch_convert<double>(F + 3 * N, (double*)area, (long long)N, h->stream)
+                            : lbm::launch_convert<float>(F + 3 * N, (float*)area, (long long)N, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "porosity field");
+        h->k64.eps_field = (const double*)area;
+        h->k32.eps_field = (const float*)area;
+    } else {
+        h->k64.eps_field = nullptr;
+        h->k32.eps_field = nullptr;
+    }
     const double* dT = nullptr;
     const double* dux = nullptr;
     const double* duy = nullptr;

@@ -71,6 +71,15 @@ struct KConst {
     float inv_scale;       // 1 / scale (a power of two)
     int* flag;             // non-finite flag (device)
     int plane32;           // plane stride as a 32-bit offset (17 planes < 2^31 elements)
+    // porosity field (nullptr: uniform eps).  With a field, K follows the
+    // Kozeny-Carman form of the Ergun permeability, K(eps) = K_ref r(eps) with
+    // r(eps) = [eps^3 / (1 - eps)^2] / [eps_ref^3 / (1 - eps_ref)^2].
+    const R* eps_field;    // [ny][nx]
+    R kc_inv_ref;          // (1 - eps_ref)^2 / eps_ref^3
+    R nu_over_Kref;        // nu / K_ref
+    R inv_sqrt_Kref;       // 1 / sqrt(K_ref)
+    R p_pref_eps;          // c_s^2 / (1 - w_0)
+    int da_inf, forch;
     // constants of the interior fast path (see interior_update)
     R inv_rho0, half_eps_ax, half_eps, p_uF, p_uu;
     R fA_ep, fA_uu, fA_tr, fA_uF, f_cu2, f_ScS, f_cucF, f_cu, f_cF;
@@ -168,15 +177,6 @@ struct Pops {
     R h[9];
 };
 
-template <class R>
-struct NodeState {
-    R th;               // T - T0
-    R ux, uy, Fx, Fy;   // velocity, total force
-    R p;
-    R Sxx, Sxy, Syy;    // shear rate
-    R gx, gy;           // grad T
-};
-
 // Role of node (x, y): interior, or a wall node with its NEES neighbours.
 struct WallInfo {
     int wall;       // 0 interior
@@ -250,133 +250,312 @@ __device__ __forceinline__ Acc pull_hsum(const KConst<R>& k, const S* __restrict
     return s;
 }
 
-// Moments of one node from its post-streaming populations.
+// ------------------------------------------------------------ dual numbers
+// Forward-mode derivatives: a value and one tangent.  The generic per-node
+// functions below are templates over the value type V (R, or Dual<R> for
+// the adjoint), so the adjoint differentiates exactly the code that runs.
 template <class R>
-__device__ __forceinline__ NodeState<R> node_moments(const KConst<R>& k, const Pops<R>& P) {
-    NodeState<R> s;
-    const R* f = P.f;
-    const R* h = P.h;
+struct Dual {
+    R v, d;
+    __host__ __device__ Dual() : v(R(0)), d(R(0)) {}
+    __host__ __device__ Dual(R v_) : v(v_), d(R(0)) {}
+    __host__ __device__ Dual(R v_, R d_) : v(v_), d(d_) {}
+};
+template <class R> __device__ __forceinline__ Dual<R> operator+(Dual<R> a, Dual<R> b) { return {a.v + b.v, a.d + b.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a, Dual<R> b) { return {a.v - b.v, a.d - b.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator*(Dual<R> a, Dual<R> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator/(Dual<R> a, Dual<R> b) {
+    const R q = a.v / b.v;
+    return {q, (a.d - q * b.d) / b.v};
+}
+template <class R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a) { return {-a.v, -a.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator+(Dual<R> a, R b) { return {a.v + b, a.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator+(R a, Dual<R> b) { return {a + b.v, b.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator-(Dual<R> a, R b) { return {a.v - b, a.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator-(R a, Dual<R> b) { return {a - b.v, -b.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator*(Dual<R> a, R b) { return {a.v * b, a.d * b}; }
+template <class R> __device__ __forceinline__ Dual<R> operator*(R a, Dual<R> b) { return {a * b.v, a * b.d}; }
+template <class R> __device__ __forceinline__ Dual<R> operator/(Dual<R> a, R b) { return {a.v / b, a.d / b}; }
+template <class R> __device__ __forceinline__ Dual<R> operator/(R a, Dual<R> b) {
+    const R q = a / b.v;
+    return {q, -q * b.d / b.v};
+}
+
+template <class R> __device__ __forceinline__ R val(R x) { return x; }
+template <class R> __device__ __forceinline__ R val(Dual<R> x) { return x.v; }
+
+// Square root of an argument that is never zero.
+template <class R> __device__ __forceinline__ R vsqrt(R x) { return sqrt(x); }
+template <class R> __device__ __forceinline__ Dual<R> vsqrt(Dual<R> x) {
+    const R r = sqrt(x.v);
+    return {r, x.d / (R(2) * r)};
+}
+// Euclidean norm from its square.  Where the vector is zero the norm is not
+// differentiable, but it only enters multiplied by the vector itself
+// (abs(v) v in the quadratic solve, abs(u) u in the Forchheimer drag), whose
+// derivative there is zero: the tangent is set to 0.
+template <class R> __device__ __forceinline__ R vnorm(R sq) { return sqrt(sq); }
+template <class R> __device__ __forceinline__ Dual<R> vnorm(Dual<R> sq) {
+    const R r = sqrt(sq.v);
+    return {r, r > R(0) ? sq.d / (R(2) * r) : R(0)};
+}
+
+// Porosity-dependent constants of one node.
+template <class V>
+struct CellC {
+    V eps, inv_eps, e_nuK, e_FK, c0, c0sq, c1, p_pref, bcoef;
+};
+
+template <class R>
+__device__ __forceinline__ R node_eps(const KConst<R>& k, int x, int y) {
+    return k.eps_field ? k.eps_field[(long long)y * k.nx + x] : k.eps;
+}
+
+// Constants at porosity eps: the run's own constants for a uniform porosity,
+// else from the Kozeny-Carman permeability K(eps) and the Ergun F_eps(eps)
+// (Sec. 2): e_nuK = eps nu/K, e_FK = eps F_eps/sqrt(K), c0 = (1 + e_nuK/2)/2,
+// c1 = e_FK/2 (Sec. 3.1).
+template <class R, class V>
+__device__ __forceinline__ CellC<V> cell_consts(const KConst<R>& k, V eps) {
+    CellC<V> c;
+    if (!k.eps_field) {
+        c.eps = V(k.eps);
+        c.inv_eps = V(k.inv_eps);
+        c.e_nuK = V(k.e_nuK);
+        c.e_FK = V(k.e_FK);
+        c.c0 = V(k.c0);
+        c.c0sq = V(k.c0sq);
+        c.c1 = V(k.c1);
+        c.p_pref = V(k.p_pref);
+        c.bcoef = V(k.bcoef);
+        return c;
+    }
+    c.eps = eps;
+    c.inv_eps = R(1) / eps;
+    if (k.da_inf) {
+        c.e_nuK = V(R(0));
+        c.e_FK = V(R(0));
+    } else {
+        const V om = R(1) - eps;
+        const V ratio = eps * eps * eps / (om * om) * k.kc_inv_ref;  // K / K_ref
+        c.e_nuK = eps * k.nu_over_Kref / ratio;
+        if (k.forch) {
+            const V Feps = R(1.75) / vsqrt(R(150) * eps * eps * eps);
+            c.e_FK = eps * Feps * k.inv_sqrt_Kref / vsqrt(ratio);
+        } else {
+            c.e_FK = V(R(0));
+        }
+    }
+    c.c0 = R(0.5) + R(0.25) * c.e_nuK;
+    c.c0sq = c.c0 * c.c0;
+    c.c1 = R(0.5) * c.e_FK;
+    c.p_pref = k.p_pref_eps * c.inv_eps;
+    c.bcoef = R(0.5) * (c.inv_eps - k.inv_sigma);
+    return c;
+}
+
+template <class V>
+struct State {
+    V th;               // T - T0
+    V ux, uy, Fx, Fy;   // velocity, total force
+    V p;
+    V Sxx, Sxy, Syy;    // shear rate
+    V gx, gy;           // grad T
+};
+
+// Moments of one node from its post-streaming populations (f[1..8], h[0..8]).
+template <class R, class V>
+__device__ __forceinline__ State<V> node_moments(const KConst<R>& k, const CellC<V>& c, const V* f,
+                                                 const V* h) {
+    State<V> s;
     // sigma T = sum g + Q/2, with sum g = sum h + sigma T0
-    R sh = h[0] + h[1] + h[2] + h[3] + h[4] + h[5] + h[6] + h[7] + h[8];
+    const V sh = h[0] + h[1] + h[2] + h[3] + h[4] + h[5] + h[6] + h[7] + h[8];
     s.th = (sh + R(0.5) * k.Q) * k.inv_sigma;
-    const R T = k.T0 + s.th;
+    const V T = k.T0 + s.th;
     // flow moments
-    const R sf = f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
-    const R mx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    const R my = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
-    const R d58 = f[5] + f[6] + f[7] + f[8];
-    const R Pxx = f[1] + f[3] + d58;
-    const R Pyy = f[2] + f[4] + d58;
-    const R Pxy = (f[5] + f[7]) - (f[6] + f[8]);
+    const V sf = f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8];
+    const V mx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const V my = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
+    const V d58 = f[5] + f[6] + f[7] + f[8];
+    const V Pxx = f[1] + f[3] + d58;
+    const V Pyy = f[2] + f[4] + d58;
+    const V Pxy = (f[5] + f[7]) - (f[6] + f[8]);
     // buoyancy, temporary velocity, quadratic solve
     const R Gx = k.ax;
-    const R Gy = k.gbeta * s.th + k.ay;
-    const R vx = mx / k.rho0 + R(0.5) * k.eps * Gx;
-    const R vy = my / k.rho0 + R(0.5) * k.eps * Gy;
-    const R vmag = sqrt(vx * vx + vy * vy);
-    const R den = k.c0 + sqrt(k.c0sq + k.c1 * vmag);
+    const V Gy = k.gbeta * s.th + k.ay;
+    const V vx = mx * k.inv_rho0 + R(0.5) * c.eps * Gx;
+    const V vy = my * k.inv_rho0 + R(0.5) * c.eps * Gy;
+    const V vmag = vnorm(vx * vx + vy * vy);
+    const V den = c.c0 + vsqrt(c.c0sq + c.c1 * vmag);
     s.ux = vx / den;
     s.uy = vy / den;
-    const R uu = s.ux * s.ux + s.uy * s.uy;
-    const R umag = sqrt(uu);
-    const R drag = k.e_nuK + k.e_FK * umag;
-    s.Fx = -drag * s.ux + k.eps * Gx;
-    s.Fy = -drag * s.uy + k.eps * Gy;
-    const R uF = s.ux * s.Fx + s.uy * s.Fy;
+    const V uu = s.ux * s.ux + s.uy * s.uy;
+    const V umag = vnorm(uu);
+    const V drag = c.e_nuK + c.e_FK * umag;
+    s.Fx = c.eps * Gx - drag * s.ux;
+    s.Fy = c.eps * Gy - drag * s.uy;
+    const V uF = s.ux * s.Fx + s.uy * s.Fy;
     // p = c_s^2/(eps (1-w0)) [sum_{i!=0} f + tau_f F_0 + rho0 s_0],
     // F_0 = -3 w0 rho0 kf u.F/eps, s_0 = -1.5 w0 |u|^2/eps, w0 = 4/9
-    const R F0 = -(R(4) / R(3)) * k.rho0 * k.kf * uF * k.inv_eps;
-    const R s0 = -(R(2) / R(3)) * uu * k.inv_eps;
-    s.p = k.p_pref * (sf + k.tau_f * F0 + k.rho0 * s0);
+    const V F0 = -(R(4) / R(3)) * k.rho0 * k.kf * uF * c.inv_eps;
+    const V s0 = -(R(2) / R(3)) * uu * c.inv_eps;
+    s.p = c.p_pref * (sf + k.tau_f * F0 + k.rho0 * s0);
     // S = [Pi - eps p I - rho0 u u/eps + (rho0/2)(uF + Fu)/eps] / (c_s^2 rho0 (A - tau_f))
-    const R re = k.rho0 * k.inv_eps;
-    const R ep = k.eps * s.p;
+    const V re = k.rho0 * c.inv_eps;
+    const V ep = c.eps * s.p;
     s.Sxx = (Pxx - ep - re * s.ux * s.ux + re * s.ux * s.Fx) * k.invD;
     s.Syy = (Pyy - ep - re * s.uy * s.uy + re * s.uy * s.Fy) * k.invD;
     s.Sxy = (Pxy - re * s.ux * s.uy + R(0.5) * re * (s.ux * s.Fy + s.Fx * s.uy)) * k.invD;
     // N = sum c (g - g^{e(0)}) + (T F + u Q/sigma)/2 with sum c g^{e(0)} = T u
-    const R nx_ = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
-    const R ny_ = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
+    const V nx_ = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+    const V ny_ = (h[2] - h[4]) + (h[5] - h[8]) + (h[6] - h[7]);
     const R qs = R(0.5) * k.Q * k.inv_sigma;
-    const R Nx = nx_ - T * s.ux + R(0.5) * T * s.Fx + qs * s.ux;
-    const R Ny = ny_ - T * s.uy + R(0.5) * T * s.Fy + qs * s.uy;
+    const V Nx = nx_ - T * s.ux + R(0.5) * T * s.Fx + qs * s.ux;
+    const V Ny = ny_ - T * s.uy + R(0.5) * T * s.Fy + qs * s.uy;
     // M = a I - b u u^T, a = -eps p/(2 rho0) + c_s^2 sigma (B - tau_T),
     // b = (1/eps - 1/sigma)/2; M^{-1} N = (N + b u (u.N)/(a - b|u|^2)) / a
-    const R a = -R(0.5) * ep / k.rho0 + k.a_const;
-    const R uN = s.ux * Nx + s.uy * Ny;
-    const R t = k.bcoef * uN / (a - k.bcoef * uu);
-    const R ia = R(1) / a;
+    const V a = k.a_const - R(0.5) * ep * k.inv_rho0;
+    const V uN = s.ux * Nx + s.uy * Ny;
+    const V t = c.bcoef * uN / (a - c.bcoef * uu);
+    const V ia = R(1) / a;
     s.gx = (Nx + t * s.ux) * ia;
     s.gy = (Ny + t * s.uy) * ia;
     return s;
 }
 
 // Equilibria and source terms of one state, direction by direction.
-template <class R>
+template <class V>
 struct EqTerms {
-    R fe[9];   // f^eq_i, i = 1..8 (index 0 unused)
-    R Fi[9];   // forcing term F_i, i = 1..8
-    R he[9];   // g^eq_i - w_i sigma T0
-    R PQ[9];   // P_i + Q_i
+    V fe[9];   // f^eq_i, i = 1..8 (index 0 unused)
+    V Fi[9];   // forcing term F_i, i = 1..8
+    V he[9];   // g^eq_i - w_i sigma T0
+    V PQ[9];   // P_i + Q_i
 };
 
-template <class R>
-__device__ __forceinline__ void eq_terms(const KConst<R>& k, const NodeState<R>& s, EqTerms<R>& e) {
-    const R T = k.T0 + s.th;
-    const R uu = s.ux * s.ux + s.uy * s.uy;
-    const R ie = k.inv_eps;
-    const R flow_c = R(3) * k.eps * s.p - R(1.5) * k.rho0 * uu * ie - R(0.5) * k.rho0 * k.A * (s.Sxx + s.Syy);
-    const R uF = s.ux * s.Fx + s.uy * s.Fy;
-    const R force_c = -R(3) * uF * ie;
-    const R pT = R(3) * T * k.eps * s.p / k.rho0;   // 3 T eps p / rho0
-    const R ug = s.ux * s.gx + s.uy * s.gy;
-    const R Wx = T * s.Fx + k.eps * s.p * s.gx / k.rho0;
-    const R Wy = T * s.Fy + k.eps * s.p * s.gy / k.rho0;
-    const R therm_c = k.sigma * s.th - R(1.5) * T * uu * ie;
+template <class R, class V>
+__device__ __forceinline__ void eq_terms(const KConst<R>& k, const CellC<V>& c, const State<V>& s,
+                                         EqTerms<V>& e) {
+    const V T = k.T0 + s.th;
+    const V uu = s.ux * s.ux + s.uy * s.uy;
+    const V ie = c.inv_eps;
+    const V flow_c = R(3) * c.eps * s.p - R(1.5) * k.rho0 * uu * ie - R(0.5) * k.rho0 * k.A * (s.Sxx + s.Syy);
+    const V uF = s.ux * s.Fx + s.uy * s.Fy;
+    const V force_c = -R(3) * uF * ie;
+    const V pT = R(3) * T * c.eps * s.p * k.inv_rho0;   // 3 T eps p / rho0
+    const V ug = s.ux * s.gx + s.uy * s.gy;
+    const V Wx = T * s.Fx + c.eps * s.p * s.gx * k.inv_rho0;
+    const V Wy = T * s.Fy + c.eps * s.p * s.gy * k.inv_rho0;
+    const V therm_c = k.sigma * s.th - R(1.5) * T * uu * ie;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const R cx = R(cx_of(i)), cy = R(cy_of(i));
         const R w = w_of<R>(i);
-        const R cu = cx * s.ux + cy * s.uy;
-        const R cF = cx * s.Fx + cy * s.Fy;
+        const V cu = cx * s.ux + cy * s.uy;
+        const V cF = cx * s.Fx + cy * s.Fy;
         if (i > 0) {
-            const R ScS = cx * cx * s.Sxx + R(2) * cx * cy * s.Sxy + cy * cy * s.Syy;
+            const V ScS = cx * cx * s.Sxx + R(2) * cx * cy * s.Sxy + cy * cy * s.Syy;
             e.fe[i] = w * (flow_c + k.rho0 * (R(3) * cu + R(4.5) * cu * cu * ie) + R(1.5) * k.rho0 * k.A * ScS);
             e.Fi[i] = w * k.rho0 * k.kf * (R(3) * cF + R(9) * cu * cF * ie + force_c);
         } else {
-            e.fe[0] = R(0);
-            e.Fi[0] = R(0);
+            e.fe[0] = V(R(0));
+            e.Fi[0] = V(R(0));
         }
-        const R cg = cx * s.gx + cy * s.gy;
+        const V cg = cx * s.gx + cy * s.gy;
         // varpi_0 = -5/9 = -(1 - w0); varpi_i = w_i otherwise
-        const R pv = (i == 0) ? -(R(5) / R(9)) * pT : w * pT;
+        const V pv = (i == 0) ? -(R(5) / R(9)) * pT : w * pT;
         e.he[i] = w * (therm_c + T * (R(3) * cu + R(4.5) * cu * cu * ie) + k.sigma * k.B * cg) + pv;
-        const R cW = cx * Wx + cy * Wy;
-        e.PQ[i] = w * k.kT * (R(3) * cW + R(6) * k.bcoef * cu * ug + (R(1) + R(3) * cu * k.inv_sigma) * k.Q);
+        const V cW = cx * Wx + cy * Wy;
+        e.PQ[i] = w * k.kT * (R(3) * cW + R(6) * c.bcoef * cu * ug + (R(1) + R(3) * cu * k.inv_sigma) * k.Q);
     }
 }
 
 // Boundary state of a wall node (Sec. 3.4): u_b, T_b, p(x_f), S(x_f),
-// grad T_b, and F at (u_b, T_b).  thff is T(x_ff) - T0 (adiabatic walls only).
-template <class R>
-__device__ __forceinline__ NodeState<R> wall_state(const KConst<R>& k, const WallInfo& w,
-                                                   const NodeState<R>& sf, R thff) {
-    NodeState<R> b = sf;
-    b.ux = k.u_bc[w.uside][0];
-    b.uy = k.u_bc[w.uside][1];
+// grad T_b, and F at (u_b, T_b) with the wall node's own porosity (cb).
+// thff is T(x_ff) - T0 (adiabatic walls), thb the Dirichlet T_b - T0.
+template <class R, class V>
+__device__ __forceinline__ State<V> wall_state(const KConst<R>& k, const CellC<V>& cb, const WallInfo& w,
+                                               const State<V>& sf, V thff, V thb) {
+    State<V> b = sf;
+    b.ux = V(k.u_bc[w.uside][0]);
+    b.uy = V(k.u_bc[w.uside][1]);
     if (w.tside >= 0) {
-        b.th = k.T_bc[w.tside] - k.T0;
+        b.th = thb;
     } else {
         // Eq. (TNEESApGra) with zero normal gradient
-        if (w.fixgx) b.gx = R(0);
-        if (w.fixgy) b.gy = R(0);
+        if (w.fixgx) b.gx = V(R(0));
+        if (w.fixgy) b.gy = V(R(0));
         b.th = (R(4) * sf.th - thff) * (R(1) / R(3));
     }
-    const R umag = sqrt(b.ux * b.ux + b.uy * b.uy);
-    const R drag = k.e_nuK + k.e_FK * umag;
-    b.Fx = -drag * b.ux + k.eps * k.ax;
-    b.Fy = -drag * b.uy + k.eps * (k.gbeta * b.th + k.ay);
+    const V umag = vnorm(b.ux * b.ux + b.uy * b.uy);
+    const V drag = cb.e_nuK + cb.e_FK * umag;
+    b.Fx = cb.eps * k.ax - drag * b.ux;
+    b.Fy = cb.eps * (k.gbeta * b.th + k.ay) - drag * b.uy;
     return b;
+}
+
+// The whole update of one node in the generic form: inputs are the 17
+// populations pulled at the source node (the node itself, or x_f for a wall
+// node), the porosity at the source and at the node, T(x_ff) - T0 and the
+// Dirichlet T_b - T0; outputs the 17 post-collision values.  Interior nodes:
+// BGK collision (Eqs. LBEeq, TEqColli).  Wall nodes: NEES rebuild
+// (Eqs. NEESVel, TNEESAp) and collision with the boundary equilibrium,
+//   f* = f^eq(x_b) + (1 - 1/tau)[f(x_f) - f^eq(x_f)] + F_i(x_b).
+template <class R, class V>
+__device__ __forceinline__ void node_update_generic(const KConst<R>& k, const WallInfo& w, const V* in,
+                                                    V eps_s, V eps_x, V thff, V thb, V* out) {
+    V f[9], h[9];
+    f[0] = V(R(0));
+#pragma unroll
+    for (int i = 1; i < 9; ++i) f[i] = in[i - 1];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = in[8 + i];
+    const CellC<V> cs = cell_consts(k, eps_s);
+    const State<V> s = node_moments(k, cs, f, h);
+    EqTerms<V> e;
+    eq_terms(k, cs, s, e);
+    if (!w.wall) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i) out[i - 1] = e.fe[i] + k.omf * (f[i] - e.fe[i]) + e.Fi[i];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) out[8 + i] = e.he[i] + k.omT * (h[i] - e.he[i]) + e.PQ[i];
+        return;
+    }
+    const CellC<V> cb = cell_consts(k, eps_x);
+    const State<V> b = wall_state(k, cb, w, s, thff, thb);
+    EqTerms<V> eb;
+    eq_terms(k, cb, b, eb);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) out[i - 1] = eb.fe[i] + k.omf * (f[i] - e.fe[i]) + eb.Fi[i];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) out[8 + i] = eb.he[i] + k.omT * (h[i] - e.he[i]) + eb.PQ[i];
+}
+
+// Fast-path constants of a node with its own porosity (porosity field).
+template <class R>
+__device__ __forceinline__ void apply_eps(KConst<R>& k, R eps) {
+    const CellC<R> c = cell_consts(k, eps);
+    const R itf = R(1) - k.omf, itT = R(1) - k.omT;
+    k.eps = eps;
+    k.inv_eps = c.inv_eps;
+    k.e_nuK = c.e_nuK;
+    k.e_FK = c.e_FK;
+    k.c0 = c.c0;
+    k.c0sq = c.c0sq;
+    k.c1 = c.c1;
+    k.p_pref = c.p_pref;
+    k.bcoef = c.bcoef;
+    k.half_eps = R(0.5) * eps;
+    k.half_eps_ax = R(0.5) * eps * k.ax;
+    k.p_uF = c.p_pref * (R(4) / R(3)) * k.rho0 * k.kf * k.tau_f * c.inv_eps;
+    k.p_uu = c.p_pref * (R(2) / R(3)) * k.rho0 * c.inv_eps;
+    k.fA_uu = R(1.5) * itf * k.rho0 * c.inv_eps;
+    k.fA_uF = R(3) * k.rho0 * k.kf * c.inv_eps;
+    k.f_cu2 = R(4.5) * itf * k.rho0 * c.inv_eps;
+    k.f_cucF = R(9) * k.rho0 * k.kf * c.inv_eps;
+    k.h_uu = itT * R(1.5) * c.inv_eps;
+    k.h_cu2 = itT * R(4.5) * c.inv_eps;
+    k.h_ug = R(6) * k.kT * c.bcoef;
+    k.h0_uu = itT * (R(4) / R(9)) * R(1.5) * c.inv_eps;
 }
 
 // Interior node of one step, fast path.  Same arithmetic as node_moments +

@@ -1,0 +1,38 @@
+// lbm_handle.h -- the single-lattice handle behind the C ABI (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "lbm_host.h"
+#include "lbm_internal.h"
+
+struct lbm_handle {
+    lbm_params prm;
+    lbm_host::Derived d;
+    lbm_host::Layout L;
+    cudaStream_t stream;
+    char* ws;
+    bool owns_ws;
+    int cur;
+    int64_t steps, launches;
+    bool nonfinite;
+    lbm::KConst<double> k64;
+    lbm::KConst<float> k32;
+    lbm::DiagConst diag;
+    std::string err;
+
+    void* buf(int i) const { return ws + L.off_buf[i]; }
+    double* fields() const { return (double*)(ws + L.off_fields); }
+    double* snap() const { return (double*)(ws + L.off_snap); }
+    double* nu() const { return (double*)(ws + L.off_nu); }
+    double* partial() const { return (double*)(ws + L.off_partial); }
+    double* out() const { return (double*)(ws + L.off_out); }
+    int* flag() const { return (int*)(ws + L.off_flag); }
+    size_t N() const { return (size_t)prm.nx * prm.ny; }
+};
+
+// Record a failure on h (or the thread's create error when h is NULL).
+lbm_status lbm_handle_fail(lbm_handle* h, lbm_status s, const std::string& m);

@@ -92,7 +92,7 @@ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 struct Layout {
     int pitch;
     size_t plane_elems, buf_bytes;
-    size_t off_buf[2], off_fields, off_snap, off_nu, off_partial, off_out, off_flag, total;
+    size_t off_buf[2], off_fields, off_snap, off_nu, off_partial, off_eps, off_out, off_flag, total;
 };
 
 inline Layout layout(const lbm_params* p) {
@@ -110,6 +110,7 @@ inline Layout layout(const lbm_params* p) {
     L.off_snap = o; o += align256(3 * N * sizeof(double));
     L.off_nu = o; o += align256((size_t)(p->nx > p->ny ? p->nx : p->ny) * sizeof(double));
     L.off_partial = o; o += align256((size_t)lbm::residual_blocks(p->nx, p->ny) * 4 * sizeof(double));
+    L.off_eps = o; o += align256(N * sizeof(double));
     L.off_out = o; o += 256;
     L.off_flag = o; o += 256;
     L.total = o;
@@ -199,6 +200,14 @@ inline lbm::KConst<R> make_kconst(const lbm_params* p, const Derived& d, const L
     k.h0_uu = R(itT * kW0 * 1.5 * ie);
     k.h0_pT = R(itT * (5.0 / 3.0) / rho0);
     k.h0_kQ = R(kW0 * kT * p->Q);
+    // porosity field support (the field pointer is set by lbm_set_fields)
+    k.eps_field = nullptr;
+    k.kc_inv_ref = R(eps < 1.0 ? (1.0 - eps) * (1.0 - eps) / (eps * eps * eps) : 0.0);
+    k.nu_over_Kref = R(nuK);
+    k.inv_sqrt_Kref = R(isinf(d.K) ? 0.0 : 1.0 / sqrt(d.K));
+    k.p_pref_eps = R(kCs2 / (1.0 - kW0));
+    k.da_inf = p->da_infinite ? 1 : 0;
+    k.forch = p->forchheimer ? 1 : 0;
     return k;
 }
 

@@ -50,6 +50,10 @@ cudaError_t launch_residual(const KConst<R>& k, const S* src, double* snap, doub
 
 long long residual_blocks(int nx, int ny);
 
+// out[i] = R(in[i]) for i < n.
+template <class R>
+cudaError_t launch_convert(const double* in, R* out, long long n, cudaStream_t st);
+
 // ---------------------------------------------------------------- batches
 // One cavity of a batch: its constants (pitch and plane relative to its own
 // planes) and the element offset of its first plane in the batch buffers.

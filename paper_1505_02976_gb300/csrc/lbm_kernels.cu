@@ -24,44 +24,47 @@ __device__ __forceinline__ void store_node(const KConst<R>& k, S* __restrict__ d
     store_planes<S, R>(dst + at, k.plane, fo, ho, k.inv_scale, dither);
 }
 
-// Boundary state of a wall node, or the node's own state.
+// Macroscopic state of node (x, y) after streaming: its own moments, or for
+// a wall node the boundary state of Sec. 3.4.
 template <class R, class S>
-__device__ __forceinline__ NodeState<R> target_state(const KConst<R>& k, const S* __restrict__ src,
-                                                     const WallInfo& w, const NodeState<R>& s) {
+__device__ __forceinline__ State<R> node_state_at(const KConst<R>& k, const S* __restrict__ src, int x, int y) {
+    const WallInfo w = classify(k, x, y);
+    const int xs = w.wall ? w.xs : x, ys = w.wall ? w.ys : y;
+    Pops<R> P;
+    pull(k, src, xs, ys, P);
+    const State<R> s = node_moments(k, cell_consts(k, node_eps(k, xs, ys)), P.f, P.h);
     if (!w.wall) return s;
     R thff = R(0);
     if (w.tside < 0) thff = (pull_hsum<R, R, S>(k, src, w.xff, w.yff) + R(0.5) * k.Q) * k.inv_sigma;
-    return wall_state(k, w, s, thff);
+    const R thb = w.tside >= 0 ? k.T_bc[w.tside] - k.T0 : R(0);
+    return wall_state(k, cell_consts(k, node_eps(k, x, y)), w, s, thff, thb);
 }
 
-// Wall node of one step: pull x_f's populations, its moments, the NEES
-// rebuild (Eqs. NEESVel, TNEESAp, TNEESApGra) and the collision with the
-// boundary equilibrium:
-//   f* = f^eq(x_b) + (1 - 1/tau)[f(x_f) - f^eq(x_f)] + F_i(x_b)   (same for g).
-// Kept out of line: only the 4(N - 1) wall threads take it.
+// Wall node of one step: the generic update of its x_f neighbour's pulled
+// populations (NEES rebuild and boundary collision, see
+// node_update_generic).  Kept out of line: only the 4(N - 1) wall threads
+// take it.
 template <class R, class S>
 __device__ __noinline__ void wall_update(const KConst<R>& k, const S* __restrict__ src,
                                          S* __restrict__ dst, int x, int y, uint32_t step) {
     const WallInfo w = classify(k, x, y);
     Pops<R> P;
     pull(k, src, w.xs, w.ys, P);
-    const NodeState<R> s = node_moments(k, P);
-    if (!(isfinite(s.th) && isfinite(s.ux) && isfinite(s.uy))) atomicOr(k.flag, 1);
-    EqTerms<R> e;
-    eq_terms(k, s, e);
-    R nf[9], nh[9];
+    R in[17], out[17];
 #pragma unroll
-    for (int i = 1; i < 9; ++i) nf[i] = P.f[i] - e.fe[i];
+    for (int i = 1; i < 9; ++i) in[i - 1] = P.f[i];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) nh[i] = P.h[i] - e.he[i];
-    const NodeState<R> b = target_state(k, src, w, s);
-    EqTerms<R> eb;
-    eq_terms(k, b, eb);
+    for (int i = 0; i < 9; ++i) in[8 + i] = P.h[i];
+    R thff = R(0);
+    if (w.tside < 0) thff = (pull_hsum<R, R, S>(k, src, w.xff, w.yff) + R(0.5) * k.Q) * k.inv_sigma;
+    const R thb = w.tside >= 0 ? k.T_bc[w.tside] - k.T0 : R(0);
+    node_update_generic(k, w, in, node_eps(k, w.xs, w.ys), node_eps(k, x, y), thff, thb, out);
+    if (!isfinite(out[0] + out[8])) atomicOr(k.flag, 1);
     R fo[9], ho[9];
 #pragma unroll
-    for (int i = 1; i < 9; ++i) fo[i] = eb.fe[i] + k.omf * nf[i] + eb.Fi[i];
+    for (int i = 1; i < 9; ++i) fo[i] = out[i - 1];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) ho[i] = eb.he[i] + k.omT * nh[i] + eb.PQ[i];
+    for (int i = 0; i < 9; ++i) ho[i] = out[8 + i];
     Dither dither((uint32_t)(y * k.pitch + x), step);
     store_node(k, dst, (long long)y * k.pitch + x, fo, ho, &dither);
 }
@@ -74,7 +77,7 @@ __device__ __forceinline__ bool is_wall(const KConst<R>& k, int x, int y) {
 
 // The fused step: one thread per node; interior nodes take the fast path,
 // wall nodes the NEES path.
-template <class R, class S>
+template <class R, class S, bool EPS_FIELD>
 __global__ void __launch_bounds__(kStepBlock, StepOccupancy<R>::blocks)
 k_step(const __grid_constant__ KConst<R> k, const S* __restrict__ src, S* __restrict__ dst, uint32_t step) {
     const int x = blockIdx.x * kStepBlock + threadIdx.x;
@@ -84,7 +87,13 @@ k_step(const __grid_constant__ KConst<R> k, const S* __restrict__ src, S* __rest
         wall_update(k, src, dst, x, y, step);
         return;
     }
-    interior_update(k, src, dst, x, y, step);
+    if constexpr (EPS_FIELD) {
+        KConst<R> kc = k;
+        apply_eps(kc, node_eps(k, x, y));
+        interior_update(kc, src, dst, x, y, step);
+    } else {
+        interior_update(k, src, dst, x, y, step);
+    }
 }
 
 template <class R, class S>
@@ -95,7 +104,7 @@ __global__ void k_init(const __grid_constant__ KConst<R> k, S* __restrict__ dst,
     const int y = blockIdx.y;
     if (x >= k.nx) return;
     const long long c = (long long)y * k.nx + x;
-    NodeState<R> s;
+    State<R> s;
     s.th = R((T ? T[c] : T_init) - double(k.T0));
     s.ux = ux ? R(ux[c]) : R(0);
     s.uy = uy ? R(uy[c]) : R(0);
@@ -104,7 +113,7 @@ __global__ void k_init(const __grid_constant__ KConst<R> k, S* __restrict__ dst,
     s.Sxx = s.Sxy = s.Syy = R(0);
     s.gx = s.gy = R(0);
     EqTerms<R> e;
-    eq_terms(k, s, e);
+    eq_terms(k, cell_consts(k, node_eps(k, x, y)), s, e);
     store_node(k, dst, (long long)y * k.pitch + x, e.fe, e.he);
 }
 
@@ -115,10 +124,7 @@ __global__ void k_moments(const __grid_constant__ KConst<R> k, const S* __restri
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= k.nx) return;
-    const WallInfo w = classify(k, x, y);
-    Pops<R> P;
-    pull(k, src, w.wall ? w.xs : x, w.wall ? w.ys : y, P);
-    const NodeState<R> s = target_state(k, src, w, node_moments(k, P));
+    const State<R> s = node_state_at(k, src, x, y);
     const long long c = (long long)y * k.nx + x;
     p[c] = double(s.p);
     ux[c] = double(s.ux);
@@ -228,10 +234,7 @@ k_residual(const __grid_constant__ KConst<R> k, const S* __restrict__ src, doubl
     const int y = blockIdx.y;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (x < k.nx) {
-        const WallInfo w = classify(k, x, y);
-        Pops<R> P;
-        pull(k, src, w.wall ? w.xs : x, w.wall ? w.ys : y, P);
-        const NodeState<R> s = target_state(k, src, w, node_moments(k, P));
+        const State<R> s = node_state_at(k, src, x, y);
         const long long N = (long long)k.nx * k.ny;
         const long long c = (long long)y * k.nx + x;
         const double ux = double(s.ux), uy = double(s.uy), T = double(k.T0) + double(s.th);
@@ -265,7 +268,21 @@ __global__ void k_reduce4(const double* __restrict__ partial, long long nb, doub
     }
 }
 
+template <class R>
+__global__ void k_convert(const double* __restrict__ in, R* __restrict__ out, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = R(in[i]);
+}
+
 // ------------------------------------------------------------------ launchers
+
+template <class R>
+cudaError_t launch_convert(const double* in, R* out, long long n, cudaStream_t st) {
+    k_convert<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+template cudaError_t launch_convert<double>(const double*, double*, long long, cudaStream_t);
+template cudaError_t launch_convert<float>(const double*, float*, long long, cudaStream_t);
 
 static dim3 row_grid(int nx, int ny, int bx) { return dim3((unsigned)((nx + bx - 1) / bx), (unsigned)ny); }
 
@@ -275,7 +292,10 @@ long long residual_blocks(int nx, int ny) {
 
 template <class R, class S>
 cudaError_t launch_step(const KConst<R>& k, const S* src, S* dst, uint32_t step, cudaStream_t st) {
-    k_step<R, S><<<row_grid(k.nx, k.ny, kStepBlock), kStepBlock, 0, st>>>(k, src, dst, step);
+    if (k.eps_field)
+        k_step<R, S, true><<<row_grid(k.nx, k.ny, kStepBlock), kStepBlock, 0, st>>>(k, src, dst, step);
+    else
+        k_step<R, S, false><<<row_grid(k.nx, k.ny, kStepBlock), kStepBlock, 0, st>>>(k, src, dst, step);
     return cudaGetLastError();
 }
 

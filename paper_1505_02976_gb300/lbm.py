@@ -29,7 +29,8 @@ EXPORTED = ("lbm_params_default", "lbm_derived", "lbm_workspace_size", "lbm_crea
             "lbm_kernel_launches", "lbm_batch_workspace_size", "lbm_batch_create",
             "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_set_fields", "lbm_batch_step",
             "lbm_batch_autotune", "lbm_batch_set_launch", "lbm_batch_sync", "lbm_batch_nusselt",
-            "lbm_batch_moments", "lbm_batch_steps_done", "lbm_batch_kernel_launches")
+            "lbm_batch_moments", "lbm_batch_steps_done", "lbm_batch_kernel_launches",
+            "lbm_adjoint")
 BATCH_MODE = {"fused": 0, "graph": 1, "per_case": 2}
 
 
@@ -92,6 +93,7 @@ def load(build_if_missing: bool = True):
     L.lbm_steps_done.restype = C.c_int64
     L.lbm_kernel_launches.argtypes = [H]
     L.lbm_kernel_launches.restype = C.c_int64
+    L.lbm_adjoint.argtypes = [H, C.c_int64, C.c_int64, C.c_int, dp, C.c_void_p, C.c_void_p]
     B = C.c_void_p
     L.lbm_batch_workspace_size.argtypes = [P, C.c_int32, C.POINTER(C.c_size_t)]
     L.lbm_batch_create.argtypes = [P, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(B)]
@@ -213,11 +215,28 @@ class Lattice:
             pass
 
     # ---- state
-    def set_fields(self, T=None, ux=None, uy=None):
-        on_dev = any(hasattr(a, "data_ptr") for a in (T, ux, uy) if a is not None)
+    def set_fields(self, T=None, ux=None, uy=None, eps_field=None):
+        """Initial state from fields (numpy arrays, or float64 CUDA tensors);
+        eps_field sets a porosity field (None: the uniform eps)."""
+        given = [a for a in (T, ux, uy, eps_field) if a is not None]
+        on_dev = any(hasattr(a, "data_ptr") for a in given)
+        if on_dev and not all(hasattr(a, "data_ptr") for a in given):
+            raise ValueError("fields must all be host arrays or all device tensors")
         conv = (lambda a: a) if on_dev else (lambda a: None if a is None else np.ascontiguousarray(a, np.float64))
-        T, ux, uy = conv(T), conv(ux), conv(uy)
-        _check(self.lib.lbm_set_fields(self.h, _ptr(T), _ptr(ux), _ptr(uy), None, int(on_dev)), self.h)
+        T, ux, uy, eps_field = conv(T), conv(ux), conv(uy), conv(eps_field)
+        _check(self.lib.lbm_set_fields(self.h, _ptr(T), _ptr(ux), _ptr(uy), _ptr(eps_field), int(on_dev)),
+               self.h)
+
+    def adjoint(self, steps: int, side="W", segment: int = 0, porosity_gradient: bool = True):
+        """Run `steps` steps, return (loss, d loss/d eps [ny, nx] or None,
+        d loss/d T_bc [4]) for loss = mean Nusselt number on `side`."""
+        k = SIDE[side] if isinstance(side, str) else int(side)
+        loss = C.c_double()
+        g_eps = np.empty((self.ny, self.nx)) if porosity_gradient else None
+        g_t = np.empty(4)
+        _check(self.lib.lbm_adjoint(self.h, int(steps), int(segment), k, C.byref(loss), _ptr(g_eps),
+                                    _ptr(g_t)), self.h)
+        return loss.value, g_eps, g_t
 
     def step(self, n: int = 1):
         _check(self.lib.lbm_step(self.h, int(n)), self.h)
