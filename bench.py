@@ -258,7 +258,44 @@ def variant_lines(device, local, warmup: int, steps: int) -> dict:
         del lat
         torch.cuda.empty_cache()
     out["batch512_fp32"] = batch_line(device, local, peak)
+    out["adjoint256_fp32"] = adjoint_line(device, local)
     return out
+
+
+def adjoint_line(device, local) -> dict:
+    """The differentiation workload: 256 x 256 cavity, Ra 1e5, porosity from
+    a seeded Gaussian random field (correlation 16 cells) in [0.3, 0.9],
+    Da 1e-3 at eps 0.6 (Kozeny-Carman), 4000 FP32 steps forward with
+    checkpoints every 64 steps, then the adjoint back to step 0: the time of
+    the whole lbm_adjoint call against the forward steps alone."""
+    import torch
+
+    from paper_1505_02976_gb300 import lbm
+    from paper_1505_02976_gb300 import workloads as W
+    n, steps = 256, 4000
+    p = W.cavity(n, 1e5, 1e-3, 0.6)
+    eps = W.gaussian_random_field(n, corr=16.0, seed=1)
+    stream = torch.cuda.Stream(device)
+    lat = lbm.Lattice(p, "f32", device=local, stream=stream)
+    lat.set_fields(eps_field=eps)
+    lat.step(20)
+    lat.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    fwd = e0.elapsed_time(e1) / 1e3
+    lat.set_fields(eps_field=eps)
+    t0 = time.perf_counter()
+    loss, g_eps, g_t = lat.adjoint(steps)
+    total = time.perf_counter() - t0
+    lat.close()
+    return {"nodes": n * n, "steps": steps, "dtype": "f32", "unit": "MLUPS",
+            "value": n * n * steps / total / 1e6, "seconds": total,
+            "forward_seconds": fwd, "forward_MLUPS": n * n * steps / fwd / 1e6,
+            "cost_vs_forward": total / fwd, "loss_nu_hot": loss,
+            "dnu_dTh": float(g_t[0]), "dnu_dTc": float(g_t[1])}
 
 
 def batch_line(device, local, peak: float) -> dict:

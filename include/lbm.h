@@ -191,6 +191,13 @@ lbm_status lbm_nusselt_noalloc(lbm_handle* h, int side, double* nu_mean);
  * replaced by the current fields.  Synchronises. */
 lbm_status lbm_residual(lbm_handle* h, double* res_u, double* res_T);
 
+/* Totals of the stored post-collision state, reduced in FP64 in a fixed
+ * order: sum_f = sum over nodes of f_1 + ... + f_8 (f_0 is not stored),
+ * sum_g = sum over nodes of g_0 + ... + g_8.  With periodic sides and Q = 0
+ * sum_g is conserved exactly by the step (sum_i g_i^eq = sigma T and
+ * sum_i P_i = 0, Sec. 3.2): the energy diagnostic.  Synchronises. */
+lbm_status lbm_totals(lbm_handle* h, double* sum_f, double* sum_g);
+
 /* The post-collision populations of the last step as float64 [9][ny][nx]
  * arrays, g absolute (not as a deviation).  f_0 is not stored by the GPU
  * path (no moment reads it: p uses sum_{i!=0} f_i, Sec. 3.1) and is

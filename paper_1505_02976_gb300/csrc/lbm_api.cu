@@ -355,6 +355,22 @@ lbm_status lbm_set_state(lbm_handle* h, const double* f, const double* g, int on
     return LBM_OK;
 }
 
+lbm_status lbm_totals(lbm_handle* h, double* sum_f, double* sum_g) {
+    if (!h || !sum_f || !sum_g) return h ? fail(h, LBM_ERR_ARG, "null output") : LBM_ERR_ARG;
+    cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        return lbm::launch_totals(k, (const S*)h->buf(h->cur), h->prm.sigma * h->d.T0, h->partial(), h->out(),
+                                  h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "totals kernels");
+    double v[4];
+    LBM_CUDA(h, cudaMemcpyAsync(v, h->out(), sizeof(v), cudaMemcpyDeviceToHost, h->stream), "totals copy");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "totals");
+    *sum_f = v[0];
+    *sum_g = v[1];
+    return LBM_OK;
+}
+
 int64_t lbm_steps_done(const lbm_handle* h) { return h ? h->steps : -1; }
 
 int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : -1; }

@@ -493,13 +493,54 @@ __device__ __forceinline__ State<V> wall_state(const KConst<R>& k, const CellC<V
     return b;
 }
 
+// out[i-1] += a_f f^eq_i + b_f F_i (i = 1..8) and out[8+i] += a_g h^eq_i +
+// b_g (P_i + Q_i) (i = 0..8): the equilibria and sources of one state
+// accumulated straight into the outputs, so no per-direction array stays
+// live (the wall path then fits the step kernel's register budget).
+template <class R, class V>
+__device__ __forceinline__ void eq_accumulate(const KConst<R>& k, const CellC<V>& c, const State<V>& s, R a_f,
+                                              R b_f, R a_g, R b_g, V* out) {
+    const V T = k.T0 + s.th;
+    const V uu = s.ux * s.ux + s.uy * s.uy;
+    const V ie = c.inv_eps;
+    const V flow_c = R(3) * c.eps * s.p - R(1.5) * k.rho0 * uu * ie - R(0.5) * k.rho0 * k.A * (s.Sxx + s.Syy);
+    const V uF = s.ux * s.Fx + s.uy * s.Fy;
+    const V force_c = -R(3) * uF * ie;
+    const V pT = R(3) * T * c.eps * s.p * k.inv_rho0;
+    const V ug = s.ux * s.gx + s.uy * s.gy;
+    const V Wx = T * s.Fx + c.eps * s.p * s.gx * k.inv_rho0;
+    const V Wy = T * s.Fy + c.eps * s.p * s.gy * k.inv_rho0;
+    const V therm_c = k.sigma * s.th - R(1.5) * T * uu * ie;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const R cx = R(cx_of(i)), cy = R(cy_of(i));
+        const R w = w_of<R>(i);
+        const V cu = cx * s.ux + cy * s.uy;
+        if (i > 0) {
+            const V cF = cx * s.Fx + cy * s.Fy;
+            const V ScS = cx * cx * s.Sxx + R(2) * cx * cy * s.Sxy + cy * cy * s.Syy;
+            const V fe = w * (flow_c + k.rho0 * (R(3) * cu + R(4.5) * cu * cu * ie) + R(1.5) * k.rho0 * k.A * ScS);
+            const V Fi = w * k.rho0 * k.kf * (R(3) * cF + R(9) * cu * cF * ie + force_c);
+            out[i - 1] = out[i - 1] + a_f * fe + b_f * Fi;
+        }
+        const V cg = cx * s.gx + cy * s.gy;
+        const V pv = (i == 0) ? -(R(5) / R(9)) * pT : w * pT;
+        const V he = w * (therm_c + T * (R(3) * cu + R(4.5) * cu * cu * ie) + k.sigma * k.B * cg) + pv;
+        const V cW = cx * Wx + cy * Wy;
+        const V PQ = w * k.kT * (R(3) * cW + R(6) * c.bcoef * cu * ug + (R(1) + R(3) * cu * k.inv_sigma) * k.Q);
+        out[8 + i] = out[8 + i] + a_g * he + b_g * PQ;
+    }
+}
+
 // The whole update of one node in the generic form: inputs are the 17
 // populations pulled at the source node (the node itself, or x_f for a wall
 // node), the porosity at the source and at the node, T(x_ff) - T0 and the
 // Dirichlet T_b - T0; outputs the 17 post-collision values.  Interior nodes:
-// BGK collision (Eqs. LBEeq, TEqColli).  Wall nodes: NEES rebuild
-// (Eqs. NEESVel, TNEESAp) and collision with the boundary equilibrium,
-//   f* = f^eq(x_b) + (1 - 1/tau)[f(x_f) - f^eq(x_f)] + F_i(x_b).
+// BGK collision (Eqs. LBEeq, TEqColli),
+//   f* = (1 - 1/tau) f + f^eq/tau + F_i.
+// Wall nodes: NEES rebuild (Eqs. NEESVel, TNEESAp) and collision with the
+// boundary equilibrium,
+//   f* = (1 - 1/tau)[f(x_f) - f^eq(x_f)] + f^eq(x_b) + F_i(x_b).
 template <class R, class V>
 __device__ __forceinline__ void node_update_generic(const KConst<R>& k, const WallInfo& w, const V* in,
                                                     V eps_s, V eps_x, V thff, V thb, V* out) {
@@ -511,23 +552,18 @@ __device__ __forceinline__ void node_update_generic(const KConst<R>& k, const Wa
     for (int i = 0; i < 9; ++i) h[i] = in[8 + i];
     const CellC<V> cs = cell_consts(k, eps_s);
     const State<V> s = node_moments(k, cs, f, h);
-    EqTerms<V> e;
-    eq_terms(k, cs, s, e);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) out[q] = k.omf * in[q];
+#pragma unroll
+    for (int q = 8; q < 17; ++q) out[q] = k.omT * in[q];
     if (!w.wall) {
-#pragma unroll
-        for (int i = 1; i < 9; ++i) out[i - 1] = e.fe[i] + k.omf * (f[i] - e.fe[i]) + e.Fi[i];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) out[8 + i] = e.he[i] + k.omT * (h[i] - e.he[i]) + e.PQ[i];
+        eq_accumulate(k, cs, s, R(1) - k.omf, R(1), R(1) - k.omT, R(1), out);
         return;
     }
+    eq_accumulate(k, cs, s, -k.omf, R(0), -k.omT, R(0), out);
     const CellC<V> cb = cell_consts(k, eps_x);
     const State<V> b = wall_state(k, cb, w, s, thff, thb);
-    EqTerms<V> eb;
-    eq_terms(k, cb, b, eb);
-#pragma unroll
-    for (int i = 1; i < 9; ++i) out[i - 1] = eb.fe[i] + k.omf * (f[i] - e.fe[i]) + eb.Fi[i];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) out[8 + i] = eb.he[i] + k.omT * (h[i] - e.he[i]) + eb.PQ[i];
+    eq_accumulate(k, cb, b, R(1), R(1), R(1), R(1), out);
 }
 
 // Fast-path constants of a node with its own porosity (porosity field).

@@ -50,6 +50,12 @@ cudaError_t launch_residual(const KConst<R>& k, const S* src, double* snap, doub
 
 long long residual_blocks(int nx, int ny);
 
+// out[0] = sum over nodes of sum_{i=1..8} f_i, out[1] = sum over nodes of
+// sum_{i=0..8} g_i (FP64, fixed order); partial as for launch_residual.
+template <class R, class S>
+cudaError_t launch_totals(const KConst<R>& k, const S* src, double sT0, double* partial, double* out,
+                          cudaStream_t st);
+
 // out[i] = R(in[i]) for i < n.
 template <class R>
 cudaError_t launch_convert(const double* in, R* out, long long n, cudaStream_t st);

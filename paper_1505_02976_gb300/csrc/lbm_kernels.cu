@@ -15,7 +15,10 @@ constexpr int kStepBlock = 128;
 // Resident blocks per SM the step kernel is compiled for: 8 x 128 threads
 // caps the FP32 kernel at 64 registers; the FP64 kernel keeps room to avoid
 // spilling.
-template <class R> struct StepOccupancy { static constexpr int blocks = 8; };
+#ifndef LBM_F32_STEP_BLOCKS
+#define LBM_F32_STEP_BLOCKS 8
+#endif
+template <class R> struct StepOccupancy { static constexpr int blocks = LBM_F32_STEP_BLOCKS; };
 template <> struct StepOccupancy<double> { static constexpr int blocks = 3; };
 
 template <class R, class S>
@@ -255,6 +258,31 @@ k_residual(const __grid_constant__ KConst<R> k, const S* __restrict__ src, doubl
     }
 }
 
+// Per-block sums of sum_{i=1..8} f_i and sum_i g_i over the stored state.
+template <class R, class S>
+__global__ void __launch_bounds__(kResBlock)
+k_totals(const __grid_constant__ KConst<R> k, const S* __restrict__ src, double sT0, double* __restrict__ partial) {
+    __shared__ double sh[kResBlock / 32];
+    const int x = blockIdx.x * kResBlock + threadIdx.x;
+    const int y = blockIdx.y;
+    double sf = 0.0, sg = 0.0;
+    if (x < k.nx) {
+        const long long at = (long long)y * k.pitch + x;
+        for (int i = 1; i < 9; ++i) sf += double(load_pop<S, R>(src + (long long)(i - 1) * k.plane + at, k.scale));
+        for (int i = 0; i < 9; ++i) sg += double(load_pop<S, R>(src + (long long)(8 + i) * k.plane + at, k.scale));
+        sg += sT0;  // sum_i w_i sigma T0
+    }
+    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    const double a = block_sum(sf, sh);
+    if (threadIdx.x == 0) partial[4 * b + 0] = a;
+    const double c = block_sum(sg, sh);
+    if (threadIdx.x == 0) {
+        partial[4 * b + 1] = c;
+        partial[4 * b + 2] = 0.0;
+        partial[4 * b + 3] = 0.0;
+    }
+}
+
 __global__ void k_reduce4(const double* __restrict__ partial, long long nb, double* __restrict__ out) {
     __shared__ double sh[kReduceBlock / 32];
     double a[4] = {0.0, 0.0, 0.0, 0.0};
@@ -348,7 +376,19 @@ cudaError_t launch_residual(const KConst<R>& k, const S* src, double* snap, doub
     return cudaGetLastError();
 }
 
+template <class R, class S>
+cudaError_t launch_totals(const KConst<R>& k, const S* src, double sT0, double* partial, double* out,
+                          cudaStream_t st) {
+    k_totals<R, S><<<row_grid(k.nx, k.ny, kResBlock), kResBlock, 0, st>>>(k, src, sT0, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce4<<<1, kReduceBlock, 0, st>>>(partial, residual_blocks(k.nx, k.ny), out);
+    return cudaGetLastError();
+}
+
 #define LBM_INSTANTIATE(R, S)                                                                        \
+    template cudaError_t launch_totals<R, S>(const KConst<R>&, const S*, double, double*, double*,  \
+                                             cudaStream_t);                                         \
     template cudaError_t launch_step<R, S>(const KConst<R>&, const S*, S*, uint32_t, cudaStream_t);           \
     template cudaError_t launch_init<R, S>(const KConst<R>&, S*, const double*, const double*,      \
                                            const double*, double, cudaStream_t);                    \
@@ -374,8 +414,13 @@ LBM_INSTANTIATE(float, __half)
 // contiguous chunk of the list (items are sorted by cavity, so a block
 // changes cavity rarely) and stages the current cavity's constants in shared
 // memory; every node then runs the same interior / wall code as k_step.
+// Small cavities have many wall nodes; the batched kernel runs better with a
+// little more register room for their out-of-line path (6 x 128 threads).
+template <class R> struct BatchOccupancy { static constexpr int blocks = 6; };
+template <> struct BatchOccupancy<double> { static constexpr int blocks = 3; };
+
 template <class R, class S, int TX>
-__global__ void __launch_bounds__(kStepBlock, StepOccupancy<R>::blocks)
+__global__ void __launch_bounds__(kStepBlock, BatchOccupancy<R>::blocks)
 k_step_batch(const BatchCavity<R>* __restrict__ cav, const BatchItem* __restrict__ items, int n_items,
              int per_block, const S* __restrict__ src, S* __restrict__ dst, uint32_t step) {
     __shared__ KConst<R> ks;

@@ -157,6 +157,6 @@ def test_autograd_function_returns_the_adjoint_gradients():
     g = lbm.Lattice(p, "f64")
     g.set_fields(eps_field=eps_np)
     loss, g_eps, g_t = g.adjoint(200)
-    assert float(nu) == pytest.approx(loss, rel=1e-12)
+    assert float(nu.detach()) == pytest.approx(loss, rel=1e-12)
     assert np.allclose(eps.grad.cpu().numpy(), 2.0 * g_eps, rtol=1e-12, atol=1e-14)
     assert np.allclose(tw.grad.cpu().numpy(), 2.0 * g_t[:2], rtol=1e-12)

@@ -261,3 +261,21 @@ def test_fp16_halves_the_population_storage():
     n16 = lbm.lbm_workspace_size(p, "f16")
     n32 = lbm.lbm_workspace_size(p, "f32")
     assert n32 - n16 >= 2 * 17 * 1024 * 1024 * 2
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_energy_total_conserved_in_periodic_box(precision):
+    """Periodic box, Q = 0: sum of g over the lattice is invariant (Sec. 3.2
+    moments), and equals the oracle's total."""
+    p = W.problem(nx=40, ny=36, bc=("periodic",) * 4, Ra=1e5, Da=1e-3, eps=0.5, sigma=1.3, tau_T=1.2)
+    fields = W.random_fields(p, seed=17, amp_u=2e-3)
+    o, g = _pair(p, precision, fields=fields)
+    sf0, sg0 = g.totals()
+    g.step(400)
+    o.run(400)
+    sf1, sg1 = g.totals()
+    tol = 1e-13 if precision == "f64" else 1e-6
+    assert sg1 == pytest.approx(sg0, rel=tol)
+    assert sg1 == pytest.approx(o.totals()[1], rel=tol)
+    tol_f = 1e-12 if precision == "f64" else 1e-5
+    assert abs(sf1 - o.f[1:].sum()) <= tol_f * np.abs(o.f[1:]).sum()
