@@ -228,6 +228,15 @@ lbm_status lbm_set_state(lbm_handle* h, const double* f, const double* g, int on
 lbm_status lbm_adjoint(lbm_handle* h, int64_t n_steps, int64_t segment, int side, double* loss,
                        double* dloss_deps, double* dloss_dTbc);
 
+/* Save (save = 1) or restore (save = 0) the complete state: populations,
+ * porosity field and step counter.  The file holds a header (format tag,
+ * precision, lattice shape, a hash of the lbm_params the handle was created
+ * with), the raw stored planes and a CRC-32 of them; a restore checks all of
+ * them and fails with LBM_ERR_ARG on any mismatch or corruption, leaving the
+ * state unchanged.  A restored run continues bit for bit as the saved one
+ * would have.  Synchronises. */
+lbm_status lbm_checkpoint(lbm_handle* h, const char* path, int save);
+
 /* Steps completed since the last lbm_set_fields. */
 int64_t lbm_steps_done(const lbm_handle* h);
 

@@ -371,6 +371,125 @@ lbm_status lbm_totals(lbm_handle* h, double* sum_f, double* sum_g) {
     return LBM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// CRC-32 (IEEE 802.3 polynomial, reflected, as in zlib), table driven.
+uint32_t crc32_update(uint32_t crc, const unsigned char* p, size_t n) {
+    static uint32_t table[256];
+    static bool ready = false;
+    if (!ready) {
+        for (uint32_t i = 0; i < 256; ++i) {
+            uint32_t c = i;
+            for (int k = 0; k < 8; ++k) c = (c & 1u) ? 0xEDB88320u ^ (c >> 1) : (c >> 1);
+            table[i] = c;
+        }
+        ready = true;
+    }
+    crc = ~crc;
+    for (size_t i = 0; i < n; ++i) crc = table[(crc ^ p[i]) & 0xFFu] ^ (crc >> 8);
+    return ~crc;
+}
+
+// FNV-1a over the problem statement, identifying the run a file belongs to.
+uint64_t params_hash(const lbm_params& p) {
+    const unsigned char* b = (const unsigned char*)&p;
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < sizeof(p); ++i) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+
+struct CkptHeader {
+    char magic[8];          // "LBMCKPT1"
+    uint32_t version;       // 1
+    int32_t precision;
+    int32_t nx, ny, pitch, has_eps;
+    int64_t steps;
+    uint64_t params_hash;
+    uint64_t payload_bytes; // populations (17 planes) then the porosity field
+};
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_checkpoint(lbm_handle* h, const char* path, int save) {
+    if (!h || !path) return h ? fail(h, LBM_ERR_ARG, "null path") : LBM_ERR_ARG;
+    const size_t es = elem_size(h->prm.precision);
+    const size_t pop_bytes = h->L.plane_elems * es * lbm::NPLANES;
+    const size_t eps_es = h->prm.precision == LBM_F64 ? 8 : 4;
+    const void* eps_dev = h->prm.precision == LBM_F64 ? (const void*)h->k64.eps_field : (const void*)h->k32.eps_field;
+    if (save) {
+        lbm_status s = lbm_sync(h);
+        if (s != LBM_OK) return s;
+        const size_t eps_bytes = eps_dev ? h->N() * eps_es : 0;
+        std::string payload(pop_bytes + eps_bytes, '\0');
+        LBM_CUDA(h, cudaMemcpy(&payload[0], h->buf(h->cur), pop_bytes, cudaMemcpyDeviceToHost), "state read");
+        if (eps_dev)
+            LBM_CUDA(h, cudaMemcpy(&payload[pop_bytes], eps_dev, eps_bytes, cudaMemcpyDeviceToHost), "field read");
+        CkptHeader hd;
+        memset(&hd, 0, sizeof(hd));
+        memcpy(hd.magic, "LBMCKPT1", 8);
+        hd.version = 1;
+        hd.precision = h->prm.precision;
+        hd.nx = h->prm.nx;
+        hd.ny = h->prm.ny;
+        hd.pitch = h->L.pitch;
+        hd.has_eps = eps_dev ? 1 : 0;
+        hd.steps = h->steps;
+        hd.params_hash = params_hash(h->prm);
+        hd.payload_bytes = payload.size();
+        const uint32_t crc = crc32_update(0, (const unsigned char*)payload.data(), payload.size());
+        FILE* f = fopen(path, "wb");
+        if (!f) return fail(h, LBM_ERR_ARG, std::string("cannot open ") + path + " for writing");
+        bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 && fwrite(payload.data(), 1, payload.size(), f) == payload.size() &&
+                  fwrite(&crc, sizeof(crc), 1, f) == 1;
+        ok = (fclose(f) == 0) && ok;
+        if (!ok) return fail(h, LBM_ERR_ARG, std::string("write failed: ") + path);
+        return LBM_OK;
+    }
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(h, LBM_ERR_ARG, std::string("cannot open ") + path);
+    CkptHeader hd;
+    if (fread(&hd, sizeof(hd), 1, f) != 1 || memcmp(hd.magic, "LBMCKPT1", 8) != 0 || hd.version != 1) {
+        fclose(f);
+        return fail(h, LBM_ERR_ARG, "not a checkpoint of this library");
+    }
+    if (hd.precision != h->prm.precision || hd.nx != h->prm.nx || hd.ny != h->prm.ny || hd.pitch != h->L.pitch ||
+        hd.params_hash != params_hash(h->prm)) {
+        fclose(f);
+        return fail(h, LBM_ERR_ARG, "checkpoint belongs to a different problem or precision");
+    }
+    const size_t expect = pop_bytes + (hd.has_eps ? h->N() * eps_es : 0);
+    if (hd.payload_bytes != expect) {
+        fclose(f);
+        return fail(h, LBM_ERR_ARG, "checkpoint payload has the wrong size");
+    }
+    std::string payload(expect, '\0');
+    uint32_t crc = 0;
+    const bool ok = fread(&payload[0], 1, expect, f) == expect && fread(&crc, sizeof(crc), 1, f) == 1;
+    fclose(f);
+    if (!ok) return fail(h, LBM_ERR_ARG, "checkpoint truncated");
+    if (crc32_update(0, (const unsigned char*)payload.data(), payload.size()) != crc)
+        return fail(h, LBM_ERR_ARG, "checkpoint corrupted (CRC-32 mismatch)");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "stream synchronise");
+    LBM_CUDA(h, cudaMemcpy(h->buf(h->cur), payload.data(), pop_bytes, cudaMemcpyHostToDevice), "state write");
+    if (hd.has_eps) {
+        char* area = h->ws + h->L.off_eps;
+        LBM_CUDA(h, cudaMemcpy(area, payload.data() + pop_bytes, h->N() * eps_es, cudaMemcpyHostToDevice), "field write");
+        h->k64.eps_field = (const double*)area;
+        h->k32.eps_field = (const float*)area;
+    } else {
+        h->k64.eps_field = nullptr;
+        h->k32.eps_field = nullptr;
+    }
+    LBM_CUDA(h, cudaMemset(h->flag(), 0, sizeof(int)), "flag reset");
+    h->steps = hd.steps;
+    h->nonfinite = false;
+    return LBM_OK;
+}
+
 int64_t lbm_steps_done(const lbm_handle* h) { return h ? h->steps : -1; }
 
 int64_t lbm_kernel_launches(const lbm_handle* h) { return h ? h->launches : -1; }

@@ -30,7 +30,7 @@ EXPORTED = ("lbm_params_default", "lbm_derived", "lbm_workspace_size", "lbm_crea
             "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_set_fields", "lbm_batch_step",
             "lbm_batch_autotune", "lbm_batch_set_launch", "lbm_batch_sync", "lbm_batch_nusselt",
             "lbm_batch_moments", "lbm_batch_steps_done", "lbm_batch_kernel_launches",
-            "lbm_adjoint", "lbm_totals")
+            "lbm_adjoint", "lbm_totals", "lbm_checkpoint")
 BATCH_MODE = {"fused": 0, "graph": 1, "per_case": 2}
 
 
@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True):
     L.lbm_kernel_launches.restype = C.c_int64
     L.lbm_adjoint.argtypes = [H, C.c_int64, C.c_int64, C.c_int, dp, C.c_void_p, C.c_void_p]
     L.lbm_totals.argtypes = [H, dp, dp]
+    L.lbm_checkpoint.argtypes = [H, C.c_char_p, C.c_int]
     B = C.c_void_p
     L.lbm_batch_workspace_size.argtypes = [P, C.c_int32, C.POINTER(C.c_size_t)]
     L.lbm_batch_create.argtypes = [P, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(B)]
@@ -269,6 +270,12 @@ class Lattice:
         ru, rT = C.c_double(), C.c_double()
         _check(self.lib.lbm_residual(self.h, C.byref(ru), C.byref(rT)), self.h)
         return ru.value, rT.value
+
+    def save(self, path: str):
+        _check(self.lib.lbm_checkpoint(self.h, os.fsencode(path), 1), self.h)
+
+    def load_checkpoint(self, path: str):
+        _check(self.lib.lbm_checkpoint(self.h, os.fsencode(path), 0), self.h)
 
     def totals(self):
         """(sum of f_1..f_8, sum of g_0..g_8) over the stored state, FP64."""
