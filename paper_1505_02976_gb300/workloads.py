@@ -90,12 +90,16 @@ CONFIG_FP32_CAVITY = dict(name="cavity2048_fp32", n=2048, Ra=1e6, Da=1e-4, eps=0
                           steps=100_000, precision="f32")
 CONFIG_FP32_ORACLE = dict(name="cavity256_fp32", n=256, Ra=1e6, Da=1e-4, eps=0.4,
                           steps=100_000, precision="f32")
-CONFIG_FP16_CAVITY = dict(name="cavity8192_fp16", n=8192, Ra=1e5, Da=1e-3, eps=0.6,
+# At 8192^2, Ra 1e5 and Ma 0.1 the derived A is -3.99, far outside the
+# range the paper tested (-0.2 <= A <= 0.4, Sec. 4.1); Ma = 0.0156 puts A at
+# -0.2 (nu_e = 0.233).
+CONFIG_FP16_CAVITY = dict(name="cavity8192_fp16", n=8192, Ra=1e5, Da=1e-3, eps=0.6, Ma=0.0156,
                           steps=2_000, precision="f16")
 
 
 def config_problem(cfg: dict, n: int | None = None) -> dict:
-    return cavity(n or cfg["n"], cfg["Ra"], cfg["Da"], cfg["eps"])
+    extra = {"Ma": cfg["Ma"]} if "Ma" in cfg else {}
+    return cavity(n or cfg["n"], cfg["Ra"], cfg["Da"], cfg["eps"], **extra)
 
 
 # --------------------------------------------------------------- fields

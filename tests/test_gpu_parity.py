@@ -234,7 +234,7 @@ def test_fp16_one_step_sampled_at_full_size():
     The GPU output is rounded to FP16 stochastically, so each value may differ
     by one FP16 step of its magnitude (2^-10 relative) plus FP32 rounding."""
     n = 8192
-    p = W.cavity(n, 1e5, 1e-3, 0.6)
+    p = W.config_problem(W.CONFIG_FP16_CAVITY)
     g = lbm.Lattice(p, "f16")
     g.set_fields(*W.random_fields(p, seed=31, amp_u=2e-3, amp_T=0.3))
     g.step(5)
