@@ -20,6 +20,8 @@ namespace {
 thread_local std::string g_batch_create_error;
 constexpr int kTiles[3] = {32, 64, 128};
 constexpr int kGraphChunk = 50;  // steps per captured graph (even: the ping-pong parity returns)
+constexpr int kMaxGrid = 1 << 16;
+constexpr double kWallCost = 4.0;  // a packed wall node costs about 4 interior nodes (out-of-line path)
 
 }  // namespace
 
@@ -36,8 +38,10 @@ struct lbm_batch {
     std::vector<long long> offset;     // element offset of each cavity's planes
     size_t buf_elems;                  // elements per population buffer
     size_t max_cells;
-    size_t off_buf[2], off_cav, off_items[3], off_fields, off_nu, off_flag;
+    size_t off_buf[2], off_cav, off_items[3], off_bounds, off_fields, off_nu, off_flag;
     int n_items[3];
+    std::vector<double> cum[3];        // cumulative estimated cost of the work lists
+    int bounds_tile, bounds_grid;      // launch shape the uploaded block ranges belong to
     int cur;
     int tile_x, grid;                  // chosen launch shape
     int sms;
@@ -52,6 +56,7 @@ struct lbm_batch {
     double* nu() const { return (double*)(ws + off_nu); }
     int* flag() const { return (int*)(ws + off_flag); }
     const lbm::BatchItem* items(int t) const { return (const lbm::BatchItem*)(ws + off_items[t]); }
+    int* bounds() const { return (int*)(ws + off_bounds); }
     size_t es() const { return precision == LBM_F64 ? 8 : 4; }
 };
 
@@ -75,14 +80,54 @@ lbm_status bcuda(lbm_batch* b, cudaError_t e, const char* what) {
 
 int tile_index(int tile_x) { return tile_x == 32 ? 0 : (tile_x == 64 ? 1 : 2); }
 
-// Work items of every cavity for tile width tile_x (tiles tile_x x 128/tile_x).
-std::vector<lbm::BatchItem> make_items(const std::vector<lbm_params>& prm, int tile_x) {
+// Number of wall nodes of a cavity (the perimeter order of the batched kernel).
+int perimeter_count(const lbm_params& p) {
+    const bool wS = p.bc[2] != LBM_BC_PERIODIC, wN = p.bc[3] != LBM_BC_PERIODIC;
+    const int rows = (wS ? p.nx : 0) + (wN ? p.nx : 0);
+    const int inner = (wN ? p.ny - 1 : p.ny) - (wS ? 1 : 0);
+    const int cols = (p.bc[0] != LBM_BC_PERIODIC ? inner : 0) + (p.bc[1] != LBM_BC_PERIODIC ? inner : 0);
+    return rows + cols;
+}
+
+// Work items of every cavity for tile width tile_x (tiles tile_x x 128/tile_x,
+// their interior nodes), then its wall nodes in chunks of 128; cum receives the
+// cumulative estimated cost.
+std::vector<lbm::BatchItem> make_items(const std::vector<lbm_params>& prm, int tile_x, std::vector<double>* cum) {
     const int ty = 128 / tile_x;
     std::vector<lbm::BatchItem> v;
-    for (int c = 0; c < (int)prm.size(); ++c)
+    double acc = 0.0;
+    if (cum) cum->assign(1, 0.0);
+    for (int c = 0; c < (int)prm.size(); ++c) {
         for (int y0 = 0; y0 < prm[c].ny; y0 += ty)
-            for (int x0 = 0; x0 < prm[c].nx; x0 += tile_x) v.push_back({c, x0, y0, 0});
+            for (int x0 = 0; x0 < prm[c].nx; x0 += tile_x) {
+                v.push_back({c, x0, y0, 0});
+                const int w = std::min(tile_x, prm[c].nx - x0) * std::min(ty, prm[c].ny - y0);
+                acc += w;
+                if (cum) cum->push_back(acc);
+            }
+        const int nw = perimeter_count(prm[c]);
+        for (int a = 0; a < nw; a += 128) {
+            const int n = std::min(128, nw - a);
+            v.push_back({c, a, n, 1});
+            acc += kWallCost * n;
+            if (cum) cum->push_back(acc);
+        }
+    }
     return v;
+}
+
+// Block ranges of equal estimated cost: bounds[k] is the first item of block k.
+std::vector<int> make_bounds(const std::vector<double>& cum, int grid) {
+    const int n = (int)cum.size() - 1;
+    std::vector<int> bnd(grid + 1);
+    const double total = cum.back();
+    int it = 0;
+    for (int k = 0; k <= grid; ++k) {
+        const double target = total * k / grid;
+        while (it < n && cum[it] < target) ++it;
+        bnd[k] = (k == grid) ? n : it;
+    }
+    return bnd;
 }
 
 // Layout of a batch; fills the offsets of b (b may be a scratch object).
@@ -112,10 +157,11 @@ lbm_status batch_layout(const lbm_params* p, int n, lbm_batch* b, std::string* w
     b->off_buf[1] = o; o += align256(elems * es);
     b->off_cav = o; o += align256((size_t)n * (prec == LBM_F64 ? sizeof(lbm::BatchCavity<double>) : sizeof(lbm::BatchCavity<float>)));
     for (int t = 0; t < 3; ++t) {
-        b->n_items[t] = (int)make_items(b->prm, kTiles[t]).size();
+        b->n_items[t] = (int)make_items(b->prm, kTiles[t], &b->cum[t]).size();
         b->off_items[t] = o;
         o += align256((size_t)b->n_items[t] * sizeof(lbm::BatchItem));
     }
+    b->off_bounds = o; o += align256((size_t)(kMaxGrid + 1) * sizeof(int));
     b->off_fields = o; o += align256(4 * b->max_cells * sizeof(double));
     b->off_nu = o; o += align256((size_t)n * sizeof(double));
     b->off_flag = o; o += 256;
@@ -149,12 +195,27 @@ cudaError_t bdispatch(lbm_batch* b, F&& fn) {
     return fn((const lbm::BatchCavity<float>*)(b->ws + b->off_cav), b->cav32, (float*)nullptr);
 }
 
+// Upload the block ranges of launch shape (tile_x, grid) (stream ordered).
+cudaError_t set_bounds(lbm_batch* b, int tile_x, int grid) {
+    if (b->bounds_tile == tile_x && b->bounds_grid == grid) return cudaSuccess;
+    const std::vector<int> bnd = make_bounds(b->cum[tile_index(tile_x)], grid);
+    cudaError_t e = cudaMemcpyAsync(b->bounds(), bnd.data(), bnd.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) {
+        b->bounds_tile = tile_x;
+        b->bounds_grid = grid;
+    }
+    return e;
+}
+
 cudaError_t fused_step(lbm_batch* b, int tile_x, int grid) {
     const int t = tile_index(tile_x);
     const int src = b->cur, dst = 1 - b->cur;
+    cudaError_t e = set_bounds(b, tile_x, grid);
+    if (e != cudaSuccess) return e;
     return bdispatch(b, [&](auto* dcav, auto&, auto* tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
-        return lbm::launch_step_batch(dcav, b->items(t), b->n_items[t], tile_x, grid, (const S*)b->buf(src),
+        return lbm::launch_step_batch(dcav, b->items(t), b->bounds(), tile_x, grid, (const S*)b->buf(src),
                                       (S*)b->buf(dst), (uint32_t)b->steps, b->stream);
     });
 }
@@ -270,7 +331,7 @@ lbm_status lbm_batch_create(const lbm_params* p, int32_t n, void* stream, void* 
     if (b->precision == LBM_F64) s = upload(b->off_cav, b->cav64.data(), n * sizeof(lbm::BatchCavity<double>), "descriptors");
     else s = upload(b->off_cav, b->cav32.data(), n * sizeof(lbm::BatchCavity<float>), "descriptors");
     for (int t = 0; t < 3 && s == LBM_OK; ++t) {
-        std::vector<lbm::BatchItem> it = make_items(b->prm, kTiles[t]);
+        std::vector<lbm::BatchItem> it = make_items(b->prm, kTiles[t], nullptr);
         s = upload(b->off_items[t], it.data(), it.size() * sizeof(lbm::BatchItem), "work list");
         if (s == LBM_OK) s = (cudaStreamSynchronize(b->stream) == cudaSuccess) ? LBM_OK : LBM_ERR_CUDA;
     }
@@ -279,7 +340,8 @@ lbm_status lbm_batch_create(const lbm_params* p, int32_t n, void* stream, void* 
     int occ = 0;
     if (b->precision == LBM_F64) occ = lbm::batch_blocks_per_sm<double, double>(32);
     else occ = lbm::batch_blocks_per_sm<float, float>(32);
-    b->grid = b->sms * std::max(occ, 1);
+    b->grid = std::min(b->sms * std::max(occ, 1), kMaxGrid);
+    b->bounds_tile = b->bounds_grid = -1;
     if (s == LBM_OK) s = lbm_batch_set_fields(b, -1, nullptr, nullptr, nullptr);
     if (s != LBM_OK) {
         g_batch_create_error = b->err;
@@ -348,6 +410,8 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t n, int mode) {
         if (b->graph_tile != b->tile_x || b->graph_grid != b->grid) drop_graphs(b);
         while (n - done >= kGraphChunk) {
             if (!b->graph[b->cur]) {
+                // the block ranges are uploaded outside the capture
+                LBM_BCUDA(b, set_bounds(b, b->tile_x, b->grid), "work ranges");
                 lbm_status s = capture(b, b->cur);
                 if (s != LBM_OK) return s;
                 b->graph_tile = b->tile_x;
@@ -382,7 +446,7 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t steps_per_candidate, int32_t
                                           : lbm::batch_blocks_per_sm<float, float>(kTiles[t]);
         occ = std::max(occ, 1);
         for (int waves = 1; waves <= 4; waves *= 2) {
-            const int g = b->sms * occ * waves;
+            const int g = std::min(b->sms * occ * waves, kMaxGrid);
             // these are real steps of the run: every launch shape computes the
             // same values, so tuning does not change the results
             cudaError_t e = fused_step(b, kTiles[t], g);
@@ -416,7 +480,8 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t steps_per_candidate, int32_t
 
 lbm_status lbm_batch_set_launch(lbm_batch* b, int32_t tile_x, int32_t grid) {
     if (!b) return LBM_ERR_ARG;
-    if ((tile_x != 32 && tile_x != 64 && tile_x != 128) || grid < 1) return bfail(b, LBM_ERR_ARG, "bad launch shape");
+    if ((tile_x != 32 && tile_x != 64 && tile_x != 128) || grid < 1 || grid > kMaxGrid)
+        return bfail(b, LBM_ERR_ARG, "bad launch shape");
     b->tile_x = tile_x;
     b->grid = grid;
     drop_graphs(b);

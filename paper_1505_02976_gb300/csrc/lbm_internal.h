@@ -70,16 +70,19 @@ struct BatchCavity {
     long long offset;
 };
 
-// Work item of the batched step: cavity index, tile origin x0, y0.
+// Work item of the batched step.  kind 0: a tile of tile_x x (128/tile_x)
+// nodes with origin (a, b) -- its interior nodes only; kind 1: the wall
+// nodes a .. a + b - 1 (b <= 128) of the cavity in perimeter order (S row,
+// N row, W column, E column, walled sides only).
 struct BatchItem {
-    int cavity, x0, y0, pad;
+    int cavity, a, b, kind;
 };
 
-// One time step of every cavity: the work list is split into equal
-// contiguous chunks, one per block of a grid of `grid` blocks; tiles are
-// tile_x x (128 / tile_x) nodes (tile_x in {32, 64, 128}).
+// One time step of every cavity: block k of the `grid` blocks takes the
+// contiguous work-list range [bounds[k], bounds[k + 1]) (ranges balanced by
+// estimated cost on the host); tile_x in {32, 64, 128}.
 template <class R, class S>
-cudaError_t launch_step_batch(const BatchCavity<R>* cav, const BatchItem* items, int n_items,
+cudaError_t launch_step_batch(const BatchCavity<R>* cav, const BatchItem* items, const int* bounds,
                               int tile_x, int grid, const S* src, S* dst, uint32_t step,
                               cudaStream_t st);
 

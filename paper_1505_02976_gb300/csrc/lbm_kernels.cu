@@ -419,16 +419,40 @@ LBM_INSTANTIATE(float, __half)
 template <class R> struct BatchOccupancy { static constexpr int blocks = 6; };
 template <> struct BatchOccupancy<double> { static constexpr int blocks = 3; };
 
+// Wall node idx of a cavity in perimeter order: S row, N row, W column, E
+// column (walled sides only; the columns skip the rows' corner nodes).
+template <class R>
+__device__ __forceinline__ void perimeter_node(const KConst<R>& k, int idx, int& x, int& y) {
+    const bool wS = k.bc[SS] != BC_PERIODIC, wN = k.bc[SN] != BC_PERIODIC;
+    const int nS = wS ? k.nx : 0, nN = wN ? k.nx : 0;
+    const int y0 = wS ? 1 : 0, y1 = wN ? k.ny - 1 : k.ny;
+    const int nW = k.bc[SW] != BC_PERIODIC ? y1 - y0 : 0;
+    if (idx < nS) { x = idx; y = 0; return; }
+    idx -= nS;
+    if (idx < nN) { x = idx; y = k.ny - 1; return; }
+    idx -= nN;
+    if (idx < nW) { x = 0; y = y0 + idx; return; }
+    idx -= nW;
+    x = k.nx - 1;
+    y = y0 + idx;
+}
+
+// Batched step: a grid of resident blocks walks a work list drawn from many
+// cavities of different size and parameters.  Each block takes one
+// contiguous, cost-balanced range of the list (items are sorted by cavity,
+// so a block changes cavity rarely) and stages the current cavity's
+// constants in shared memory.  Interior tiles and packed wall nodes are
+// separate items, so the out-of-line wall path never stalls a warp of
+// interior nodes.
 template <class R, class S, int TX>
 __global__ void __launch_bounds__(kStepBlock, BatchOccupancy<R>::blocks)
-k_step_batch(const BatchCavity<R>* __restrict__ cav, const BatchItem* __restrict__ items, int n_items,
-             int per_block, const S* __restrict__ src, S* __restrict__ dst, uint32_t step) {
+k_step_batch(const BatchCavity<R>* __restrict__ cav, const BatchItem* __restrict__ items,
+             const int* __restrict__ bounds, const S* __restrict__ src, S* __restrict__ dst, uint32_t step) {
     __shared__ KConst<R> ks;
     __shared__ long long off;
-    constexpr int TY = kStepBlock / TX;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    const int begin = blockIdx.x * per_block;
-    const int end = min(begin + per_block, n_items);
+    const int begin = bounds[blockIdx.x];
+    const int end = bounds[blockIdx.x + 1];
     int cur = -1;
     for (int it = begin; it < end; ++it) {
         const BatchItem w = items[it];
@@ -441,13 +465,15 @@ k_step_batch(const BatchCavity<R>* __restrict__ cav, const BatchItem* __restrict
             __syncthreads();
             cur = w.cavity;
         }
-        const int x = w.x0 + tx, y = w.y0 + ty;
-        (void)TY;
-        if (x < ks.nx && y < ks.ny) {
-            const S* s = src + off;
-            S* d = dst + off;
-            if (is_wall(ks, x, y)) wall_update(ks, s, d, x, y, step);
-            else interior_update(ks, s, d, x, y, step);
+        const S* s = src + off;
+        S* d = dst + off;
+        if (w.kind == 0) {
+            const int x = w.a + tx, y = w.b + ty;
+            if (x < ks.nx && y < ks.ny && !is_wall(ks, x, y)) interior_update(ks, s, d, x, y, step);
+        } else if ((int)threadIdx.x < w.b) {
+            int x, y;
+            perimeter_node(ks, w.a + (int)threadIdx.x, x, y);
+            wall_update(ks, s, d, x, y, step);
         }
     }
 }
@@ -480,14 +506,13 @@ __global__ void k_nusselt_batch(const BatchCavity<R>* __restrict__ cav, const S*
 }
 
 template <class R, class S>
-cudaError_t launch_step_batch(const BatchCavity<R>* cav, const BatchItem* items, int n_items, int tile_x,
+cudaError_t launch_step_batch(const BatchCavity<R>* cav, const BatchItem* items, const int* bounds, int tile_x,
                               int grid, const S* src, S* dst, uint32_t step, cudaStream_t st) {
-    if (grid < 1 || n_items < 1) return cudaErrorInvalidValue;
-    const int per_block = (n_items + grid - 1) / grid;
+    if (grid < 1) return cudaErrorInvalidValue;
     switch (tile_x) {
-    case 32: k_step_batch<R, S, 32><<<grid, kStepBlock, 0, st>>>(cav, items, n_items, per_block, src, dst, step); break;
-    case 64: k_step_batch<R, S, 64><<<grid, kStepBlock, 0, st>>>(cav, items, n_items, per_block, src, dst, step); break;
-    case 128: k_step_batch<R, S, 128><<<grid, kStepBlock, 0, st>>>(cav, items, n_items, per_block, src, dst, step); break;
+    case 32: k_step_batch<R, S, 32><<<grid, kStepBlock, 0, st>>>(cav, items, bounds, src, dst, step); break;
+    case 64: k_step_batch<R, S, 64><<<grid, kStepBlock, 0, st>>>(cav, items, bounds, src, dst, step); break;
+    case 128: k_step_batch<R, S, 128><<<grid, kStepBlock, 0, st>>>(cav, items, bounds, src, dst, step); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -511,8 +536,8 @@ int batch_blocks_per_sm(int tile_x) {
 }
 
 #define LBM_INSTANTIATE_BATCH(R, S)                                                                  \
-    template cudaError_t launch_step_batch<R, S>(const BatchCavity<R>*, const BatchItem*, int, int, \
-                                                 int, const S*, S*, uint32_t, cudaStream_t);        \
+    template cudaError_t launch_step_batch<R, S>(const BatchCavity<R>*, const BatchItem*, const int*, \
+                                                 int, int, const S*, S*, uint32_t, cudaStream_t);    \
     template cudaError_t launch_nusselt_batch<R, S>(const BatchCavity<R>*, int, const S*, int,      \
                                                     double*, cudaStream_t);                         \
     template int batch_blocks_per_sm<R, S>(int);
