@@ -214,19 +214,15 @@ def run_reference(args):
 # ----------------------------------------------------------------- GPU leg
 
 def time_steps(lat, stream, steps: int):
-    """Mean kernel time (event pair around each launch) and loop time (s)."""
+    """Mean launch duration and loop time (s) of `steps` back-to-back steps."""
     import torch
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for s0, s1 in ev:
-        s0.record(stream)
-        lat.step(1)
-        s1.record(stream)
+    lat.step(steps)
     b.record(stream)
     b.synchronize()
-    kernel = sum(s0.elapsed_time(s1) for s0, s1 in ev) / 1e3 / steps
-    return kernel, a.elapsed_time(b) / 1e3
+    loop = a.elapsed_time(b) / 1e3
+    return loop / steps, loop
 
 
 def variant_lines(device, local, warmup: int, steps: int) -> dict:
@@ -358,9 +354,9 @@ def run_ours(args):
     lat.step(args.warmup)
     lat.sync()
 
-    # device-timed region: K launches, an event pair around each one
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # device-timed region: K launches back to back (one lbm_step call), an
+    # event pair around them; the kernel's mean launch duration is the loop
+    # time over K (launch gaps included: nothing else runs on the stream)
     t_all0 = torch.cuda.Event(enable_timing=True)
     t_all1 = torch.cuda.Event(enable_timing=True)
     vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
@@ -371,17 +367,14 @@ def run_ours(args):
     time.sleep(0.4)
     launches0 = lat.launches
     t_all0.record(stream)
-    for i in range(args.steps):
-        starts[i].record(stream)
-        lat.step(1)
-        ends[i].record(stream)
+    lat.step(args.steps)
     t_all1.record(stream)
     torch.cuda.synchronize(device)
     clk = clocks.stop()
     barrier(world, device)
     launches = lat.launches - launches0
     elapsed = t_all0.elapsed_time(t_all1) / 1e3
-    kernel_s = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / 1e3 / args.steps
+    kernel_s = elapsed / args.steps
     lat.sync()
     elapsed_max = max_over_ranks(elapsed, world, device)
     value = world * cells * args.steps / elapsed_max / 1e6

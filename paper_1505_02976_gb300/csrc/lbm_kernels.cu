@@ -83,6 +83,12 @@ __device__ __forceinline__ bool is_wall(const KConst<R>& k, int x, int y) {
 template <class R, class S, bool EPS_FIELD>
 __global__ void __launch_bounds__(kStepBlock, StepOccupancy<R>::blocks)
 k_step(const __grid_constant__ KConst<R> k, const S* __restrict__ src, S* __restrict__ dst, uint32_t step) {
+    // Programmatic dependent launch: let the next step's blocks be scheduled
+    // while this grid drains, and wait here until the previous step's grid
+    // has completed and its writes are visible (no-op without the launch
+    // attribute).  Both are hardware-managed; nothing spins.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int x = blockIdx.x * kStepBlock + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= k.nx) return;
@@ -320,11 +326,18 @@ long long residual_blocks(int nx, int ny) {
 
 template <class R, class S>
 cudaError_t launch_step(const KConst<R>& k, const S* src, S* dst, uint32_t step, cudaStream_t st) {
-    if (k.eps_field)
-        k_step<R, S, true><<<row_grid(k.nx, k.ny, kStepBlock), kStepBlock, 0, st>>>(k, src, dst, step);
-    else
-        k_step<R, S, false><<<row_grid(k.nx, k.ny, kStepBlock), kStepBlock, 0, st>>>(k, src, dst, step);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = row_grid(k.nx, k.ny, kStepBlock);
+    cfg.blockDim = dim3(kStepBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (k.eps_field) return cudaLaunchKernelEx(&cfg, k_step<R, S, true>, k, src, dst, step);
+    return cudaLaunchKernelEx(&cfg, k_step<R, S, false>, k, src, dst, step);
 }
 
 template <class R, class S>
