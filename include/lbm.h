@@ -82,7 +82,11 @@ typedef enum {
  *   B      = tau_T - 1/2 - alpha_e / (sigma c_s^2)
  *   K      = Da L^2                       (Sec. 2)
  * F_eps = 1.75 / sqrt(150 eps^3) (Ergun) when forchheimer = 1, else 0.
- * T0 = (Th + Tc) / 2 is the buoyancy reference and the thermal rest state;
+ *   T0     = (Th + Tc) / 2                (buoyancy reference and thermal rest
+ *            state; the heat-generating cavity of Sec. 4.3 puts it at T_c)
+ *   Q      = Ra_I alpha_e (Th - Tc) / (Ra L^2)   (internal heat source,
+ *            Sec. 4.4; with Ra = Ra_I and Th - Tc = Q L^2 / alpha_e it is the
+ *            scaling of Sec. 4.3)
  * Th - Tc normalises the Nusselt number. */
 typedef struct {
     int32_t nx, ny;          /* nodes, wall nodes included; >= 4 across walls */
@@ -97,6 +101,8 @@ typedef struct {
     double L, nu, alpha_e, gbeta, A, B, K;   /* NaN = derive */
     double T_bc[4];          /* Dirichlet wall temperature per side */
     double u_bc[4][2];       /* wall velocity per side */
+    double T0;               /* NaN = derive */
+    double Ra_I;             /* internal Rayleigh number (used when Q is NaN) */
 } lbm_params;
 
 /* Fill p with the paper's defaults (Sec. 4): the 32 x 32 porous cavity,
@@ -106,11 +112,11 @@ typedef struct {
 lbm_status lbm_params_default(lbm_params* p);
 
 /* Derived lattice constants of p, in this order:
- * L, T0, dT, U, gbeta, nu, nu_e, alpha_e, A, B, K, F_eps (12 doubles).
+ * L, T0, dT, U, gbeta, nu, nu_e, alpha_e, A, B, K, F_eps, Q (13 doubles).
  * Returns LBM_ERR_PARAM_RANGE when the parameters are outside the range the
  * model admits: 0 < eps <= 1, tau > 1/2, A < tau_f - 1/2, B < tau_T - 1/2
  * (Sec. 4), sigma > 0, rho0 > 0. */
-lbm_status lbm_derived(const lbm_params* p, double out[12]);
+lbm_status lbm_derived(const lbm_params* p, double out[13]);
 
 /* Bytes of device workspace a handle for p needs (two population buffers,
  * field staging, reduction scratch, residual snapshot). */
@@ -144,6 +150,23 @@ const char* lbm_last_error(const lbm_handle* h);
 lbm_status lbm_set_fields(lbm_handle* h, const double* T, const double* ux,
                           const double* uy, const double* eps_field,
                           int on_device);
+
+/* Stream function of the current velocity field (the u_x of lbm_moments):
+ * u_x = d psi / dy, psi = 0 along the row y = 0, integrated up each column
+ * by the trapezoid rule, psi(x, y) = psi(x, y - 1) + (u_x(x, y - 1) +
+ * u_x(x, y)) / 2 in lattice units.  The paper reports the extreme of psi
+ * (Sec. 4.3, Table 3, normalised there by L sqrt(g beta dT L)) without
+ * stating its discretisation.  psi: nx * ny doubles [y][x], host or device
+ * (on_device), or NULL; range: host array receiving min and max of psi, or
+ * NULL.  Host outputs: the call synchronises. */
+lbm_status lbm_stream_function(lbm_handle* h, double* psi, int on_device, double range[2]);
+
+/* External acceleration profile: a_y(y) = ay[y] is added to the uniform a_y
+ * of the parameters in G = g beta (T - T0) j + a (Sec. 2), one value per
+ * row y = 0..ny-1, host memory (copied; NULL removes the profile).  The
+ * mixed-convection channel of Sec. 4.1 is driven by such a profile.
+ * Synchronises. */
+lbm_status lbm_set_force_profile(lbm_handle* h, const double* ay);
 
 /* Advance n >= 0 time steps (stream, rebuild walls, collide; one kernel
  * launch per step).  Asynchronous on the handle's stream.  Returns
@@ -234,7 +257,8 @@ lbm_status lbm_adjoint(lbm_handle* h, int64_t n_steps, int64_t segment, int side
  * with), the raw stored planes and a CRC-32 of them; a restore checks all of
  * them and fails with LBM_ERR_ARG on any mismatch or corruption, leaving the
  * state unchanged.  A restored run continues bit for bit as the saved one
- * would have.  Synchronises. */
+ * would have.  The force profile of lbm_set_force_profile is not part of the
+ * file: set it again on the restoring handle.  Synchronises. */
 lbm_status lbm_checkpoint(lbm_handle* h, const char* path, int save);
 
 /* Steps completed since the last lbm_set_fields. */

@@ -43,6 +43,7 @@ class _Problem(C.Structure):
         ("L", C.c_double), ("nu", C.c_double), ("alpha_e", C.c_double), ("gbeta", C.c_double),
         ("A", C.c_double), ("B", C.c_double), ("K", C.c_double),
         ("T_bc", C.c_double * 4), ("u_bc", (C.c_double * 2) * 4),
+        ("T0", C.c_double), ("Ra_I", C.c_double),
     ]
 
 
@@ -90,7 +91,9 @@ def lib():
         L.orc_gradients.argtypes = [P, vp, dp, dp, dp, dp, dp, dp, dp]
         L.orc_nusselt.argtypes = [P, dp, C.c_int, vp, C.POINTER(C.c_double)]
         L.orc_residual.argtypes = [C.c_int64, dp, dp, dp, dp, dp, dp, dp]
+        L.orc_stream_function.argtypes = [C.c_int, C.c_int, dp, dp]
         L.orc_totals.argtypes = [P, dp, dp, dp]
+        L.orc_set_ay_profile.argtypes = [vp, C.c_int]
         _lib = L
     return _lib
 
@@ -110,6 +113,7 @@ def cs_lib():
         L.orc_run.argtypes = [P, vp, cp, cp, C.c_int64]
         L.orc_moments.argtypes = [P, vp, cp, cp, vp, vp, vp, vp]
         L.orc_nusselt.argtypes = [P, cp, C.c_int, vp, vp]
+        L.orc_set_ay_profile.argtypes = [vp, C.c_int]
         _cs_lib = L
     return _cs_lib
 
@@ -163,6 +167,16 @@ def nusselt_gradient(p: dict, steps: int, eps_field, cells, sides=("W", "E"), h:
     return np.array(d_eps), d_t
 
 
+def set_ay_profile(ay, complex_build: bool = False):
+    """External acceleration a_y(y) per row (None: none) for the next calls."""
+    L = cs_lib() if complex_build else lib()
+    if ay is None:
+        L.orc_set_ay_profile(None, 0)
+    else:
+        a = np.ascontiguousarray(ay, dtype=np.float64)
+        L.orc_set_ay_profile(a.ctypes.data_as(C.c_void_p), a.size)
+
+
 def _nan_or(v):
     return float("nan") if v is None else float(v)
 
@@ -175,9 +189,9 @@ def problem_struct(p: dict) -> _Problem:
     s.forchheimer = int(p["forchheimer"])
     s.da_infinite = int(p["da_infinite"])
     for name in ("Ra", "Pr", "Da", "J", "eps", "sigma", "Ma", "tau_f", "tau_T", "Th", "Tc",
-                 "T_init", "rho0", "Q", "ax", "ay"):
+                 "T_init", "rho0", "Q", "ax", "ay", "Ra_I"):
         setattr(s, name, float(p[name]))
-    for name in ("L", "nu", "alpha_e", "gbeta", "A", "B", "K"):
+    for name in ("L", "nu", "alpha_e", "gbeta", "A", "B", "K", "T0"):
         setattr(s, name, _nan_or(p[name]))
     for k in range(4):
         s.T_bc[k] = float(p["T_bc"][k])
@@ -201,11 +215,11 @@ def lattice():
     return cx, cy, w, varpi
 
 
-DERIVED_KEYS = ("L", "T0", "dT", "U", "gbeta", "nu", "nu_e", "alpha_e", "A", "B", "K", "Feps")
+DERIVED_KEYS = ("L", "T0", "dT", "U", "gbeta", "nu", "nu_e", "alpha_e", "A", "B", "K", "Feps", "Q")
 
 
 def derived(p: dict) -> dict:
-    out = np.zeros(12)
+    out = np.zeros(13)
     s = problem_struct(p)
     rc = lib().orc_derived_values(C.byref(s), out)
     if rc:
@@ -252,11 +266,21 @@ def residual(ux, uy, T, ux0, uy0, T0):
     return float(out[0]), float(out[1])
 
 
+def stream_function(ux):
+    """psi [ny][nx] of u_x [ny][nx] (zero on row 0, trapezoid rule up the columns)."""
+    u = _c64(ux)
+    ny, nx = u.shape
+    psi = np.zeros((ny, nx))
+    lib().orc_stream_function(nx, ny, u, psi)
+    return psi
+
+
 class Oracle:
     """A lattice advanced by the oracle.  State: post-collision populations
     f[9][ny][nx], g[9][ny][nx] (float64)."""
 
-    def __init__(self, p: dict, T=None, ux=None, uy=None, eps_field=None):
+    def __init__(self, p: dict, T=None, ux=None, uy=None, eps_field=None, ay_profile=None):
+        self.ay_profile = None if ay_profile is None else np.ascontiguousarray(ay_profile, np.float64)
         self.p = dict(p)
         self.s = problem_struct(p)
         self.nx, self.ny = int(p["nx"]), int(p["ny"])
@@ -279,6 +303,7 @@ class Oracle:
         o.s = problem_struct(p)
         o.nx, o.ny = int(p["nx"]), int(p["ny"])
         o.eps_field = _c64(eps_field)
+        o.ay_profile = None
         o.steps = 0
         derived(p)  # validates the problem
         if copy:
@@ -293,6 +318,7 @@ class Oracle:
         self.g = np.ascontiguousarray(g, dtype=np.float64).copy()
 
     def run(self, n: int):
+        set_ay_profile(self.ay_profile)
         rc = lib().orc_run(C.byref(self.s), _ptr(self.eps_field), self.f, self.g, int(n))
         if rc:
             raise RuntimeError(f"oracle run failed (code {rc})")
@@ -300,6 +326,7 @@ class Oracle:
         return self
 
     def update_nodes(self, xs, ys):
+        set_ay_profile(self.ay_profile)
         xs = np.ascontiguousarray(xs, np.int32); ys = np.ascontiguousarray(ys, np.int32)
         fo = np.zeros((xs.size, 9)); go = np.zeros((xs.size, 9))
         lib().orc_update_nodes(C.byref(self.s), _ptr(self.eps_field), self.f, self.g,
@@ -307,6 +334,7 @@ class Oracle:
         return fo, go
 
     def moments(self):
+        set_ay_profile(self.ay_profile)
         shape = (self.ny, self.nx)
         p = np.zeros(shape); ux = np.zeros(shape); uy = np.zeros(shape); T = np.zeros(shape)
         lib().orc_moments(C.byref(self.s), _ptr(self.eps_field), self.f, self.g,
@@ -314,6 +342,7 @@ class Oracle:
         return dict(p=p, ux=ux, uy=uy, T=T)
 
     def gradients(self):
+        set_ay_profile(self.ay_profile)
         shape = (self.ny, self.nx)
         out = [np.zeros(shape) for _ in range(5)]
         lib().orc_gradients(C.byref(self.s), _ptr(self.eps_field), self.f, self.g, *out)

@@ -126,18 +126,40 @@ typedef struct {
     double nu, alpha_e, gbeta, A, B, K;  /* overrides; NaN: derive */
     double T_bc[4];                      /* Dirichlet wall temperature per side */
     double u_bc[4][2];                   /* wall velocity per side */
+    double T0;                           /* buoyancy reference; NaN: (Th + Tc) / 2 */
+    double Ra_I;                         /* internal Rayleigh number, for Q = NaN */
 } orc_problem;
 
 /* Lattice constants derived from the problem statement. */
 typedef struct {
-    double L, T0, dT, U, gbeta, nu, nu_e, alpha_e, A, B, K, Feps;
+    double L, T0, dT, U, gbeta, nu, nu_e, alpha_e, A, B, K, Feps, Q;
     double kappa_f, kappa_T; /* (1 - 1/(2 tau)) */
 } orc_derived;
 
-/* Porosity-dependent constants of one node. */
+/* Porosity-dependent constants of one node, and the y-component of the
+ * external acceleration a at the node's row. */
 typedef struct {
     real_t eps, nu_over_K, Feps_over_sqrtK, c0, c1;
+    double ay;
 } orc_cell;
+
+/* Optional external acceleration a_y(y) added to the problem's uniform a_y,
+ * one value per row (the mixed-convection channel of Sec. 4.1 drives its
+ * flow with such a profile).  Test infrastructure: one profile at a time. */
+static double *g_ay_profile = NULL;
+static int g_ay_rows = 0;
+int orc_set_ay_profile(const double *ay, int ny) {
+    free(g_ay_profile);
+    g_ay_profile = NULL;
+    g_ay_rows = 0;
+    if (ay && ny > 0) {
+        g_ay_profile = (double *)malloc(sizeof(double) * (size_t)ny);
+        if (!g_ay_profile) return 100;
+        memcpy(g_ay_profile, ay, sizeof(double) * (size_t)ny);
+        g_ay_rows = ny;
+    }
+    return 0;
+}
 
 /* Everything a node update needs. */
 typedef struct {
@@ -163,7 +185,7 @@ int orc_derive(const orc_problem *pb, orc_derived *d) {
     lattice_init();
     memset(d, 0, sizeof(*d));
     d->L = is_nan(pb->L) ? (real_t)(pb->nx - 1) : pb->L;
-    d->T0 = 0.5 * (pb->Th + pb->Tc);
+    d->T0 = is_nan(pb->T0) ? 0.5 * (pb->Th + pb->Tc) : pb->T0;
     d->dT = pb->Th - pb->Tc;
     d->U = pb->Ma * RSQRT(CS2);
     if (!is_nan(pb->gbeta)) d->gbeta = pb->gbeta;
@@ -180,6 +202,8 @@ int orc_derive(const orc_problem *pb, orc_derived *d) {
     if (pb->da_infinite) d->K = INFINITY;
     else d->K = is_nan(pb->K) ? pb->Da * d->L * d->L : pb->K;
     d->Feps = pb->forchheimer ? 1.75 / RSQRT(150.0 * pb->eps * pb->eps * pb->eps) : 0.0;
+    /* internal heat source of Sec. 4.4, Q = Ra_I alpha_e dT / (Ra L^2) */
+    d->Q = is_nan(pb->Q) ? pb->Ra_I * d->alpha_e * d->dT / (pb->Ra * d->L * d->L) : pb->Q;
     d->kappa_f = 1.0 - 1.0 / (2.0 * pb->tau_f);
     d->kappa_T = 1.0 - 1.0 / (2.0 * pb->tau_T);
     /* admissibility (Sec. 4): 0 < eps <= 1, tau > 1/2, A < tau_f - 1/2,
@@ -215,10 +239,17 @@ static void cell_constants(const orc_ctx *cx, real_t eps, orc_cell *c) {
     c->Feps_over_sqrtK = isinf(RE(K)) ? 0.0 : Feps / RSQRT(K);
     c->c0 = 0.5 * (1.0 + eps * 0.5 * c->nu_over_K);
     c->c1 = eps * 0.5 * c->Feps_over_sqrtK;
+    c->ay = pb->ay;
 }
 
 static real_t node_eps(const orc_ctx *cx, int x, int y) {
     return cx->eps_field ? cx->eps_field[(size_t)y * cx->pb->nx + x] : cx->pb->eps;
+}
+
+/* Constants of node (x, y): its porosity and its row's a_y. */
+static void node_cell(const orc_ctx *cx, int x, int y, orc_cell *c) {
+    cell_constants(cx, node_eps(cx, x, y), c);
+    if (g_ay_profile && y < g_ay_rows) c->ay = cx->pb->ay + g_ay_profile[y];
 }
 
 /* ------------------------------------------------ per-direction functions */
@@ -306,14 +337,14 @@ static void thermal_P(const orc_ctx *cx, const orc_cell *c, real_t T, const real
 
 /* Source Q_i of Sec. 3.2. */
 static void thermal_Q(const orc_ctx *cx, const real_t u[2], real_t out[9]) {
-    real_t sigma = cx->pb->sigma, kT = cx->d.kappa_T, Q = cx->pb->Q;
+    real_t sigma = cx->pb->sigma, kT = cx->d.kappa_T, Q = cx->d.Q;
     for (int i = 0; i < 9; ++i) out[i] = WGT[i] * kT * (1.0 + dot_c(i, u) / (sigma * CS2)) * Q;
 }
 
 /* Total force, Eq. (ForceEq), with G = g beta (T - T0) j + a. */
 static void total_force(const orc_ctx *cx, const orc_cell *c, real_t T, const real_t u[2],
                         real_t F[2]) {
-    real_t G[2] = {cx->pb->ax, cx->d.gbeta * (T - cx->d.T0) + cx->pb->ay};
+    real_t G[2] = {cx->pb->ax, cx->d.gbeta * (T - cx->d.T0) + c->ay};
     real_t umag = RSQRT(u[0] * u[0] + u[1] * u[1]);
     for (int a = 0; a < 2; ++a)
         F[a] = -c->eps * c->nu_over_K * u[a] - c->eps * c->Feps_over_sqrtK * umag * u[a] +
@@ -353,9 +384,9 @@ static void node_moments(const orc_ctx *cx, const orc_cell *c, const real_t fs[9
     /* sigma T = sum_i g_i + (dt/2) Q */
     real_t sg = 0.0;
     for (int i = 0; i < 9; ++i) sg += gs[i];
-    m->T = (sg + 0.5 * pb->Q) / sigma;
+    m->T = (sg + 0.5 * cx->d.Q) / sigma;
     /* v = sum_i c_i f_i / rho0 + (dt/2) eps G */
-    real_t G[2] = {pb->ax, cx->d.gbeta * (m->T - cx->d.T0) + pb->ay};
+    real_t G[2] = {pb->ax, cx->d.gbeta * (m->T - cx->d.T0) + c->ay};
     real_t v[2] = {0.0, 0.0};
     for (int i = 0; i < 9; ++i) { v[0] += CX[i] * fs[i]; v[1] += CY[i] * fs[i]; }
     for (int a = 0; a < 2; ++a) v[a] = v[a] / rho0 + 0.5 * eps * G[a];
@@ -385,7 +416,7 @@ static void node_moments(const orc_ctx *cx, const orc_cell *c, const real_t fs[9
     thermal_eq(cx, c, m->T, m->u, m->p, g0, 0, ge0);
     real_t N[2] = {0.0, 0.0};
     for (int i = 0; i < 9; ++i) { N[0] += CX[i] * (gs[i] - ge0[i]); N[1] += CY[i] * (gs[i] - ge0[i]); }
-    for (int a = 0; a < 2; ++a) N[a] += 0.5 * (m->T * m->F[a] + m->u[a] * pb->Q / sigma);
+    for (int a = 0; a < 2; ++a) N[a] += 0.5 * (m->T * m->F[a] + m->u[a] * cx->d.Q / sigma);
     real_t M[2][2];
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
@@ -466,7 +497,7 @@ static void node_state(const orc_ctx *cx, const real_t *f, const real_t *g, int 
     orc_wall w;
     classify(cx, x, y, &w);
     orc_cell c;
-    cell_constants(cx, node_eps(cx, x, y), &c);
+    node_cell(cx, x, y, &c);
     if (!w.wall) {
         real_t fs[9], gs[9];
         for (int i = 0; i < 9; ++i) { fs[i] = pull(cx, f, i, x, y); gs[i] = pull(cx, g, i, x, y); }
@@ -476,7 +507,7 @@ static void node_state(const orc_ctx *cx, const real_t *f, const real_t *g, int 
     }
     /* state at x_f from its own post-streaming populations */
     orc_cell cf;
-    cell_constants(cx, node_eps(cx, w.xf, w.yf), &cf);
+    node_cell(cx, w.xf, w.yf, &cf);
     real_t ff[9], gf[9];
     for (int i = 0; i < 9; ++i) { ff[i] = pull(cx, f, i, w.xf, w.yf); gf[i] = pull(cx, g, i, w.xf, w.yf); }
     orc_state sf;
@@ -492,7 +523,7 @@ static void node_state(const orc_ctx *cx, const real_t *f, const real_t *g, int 
     } else {
         /* Eq. (TNEESApGra) with a zero prescribed normal gradient */
         orc_cell cff;
-        cell_constants(cx, node_eps(cx, w.xff, w.yff), &cff);
+        node_cell(cx, w.xff, w.yff, &cff);
         real_t fff[9], gff[9];
         for (int i = 0; i < 9; ++i) { fff[i] = pull(cx, f, i, w.xff, w.yff); gff[i] = pull(cx, g, i, w.xff, w.yff); }
         orc_state sff;
@@ -526,7 +557,7 @@ static void node_update(const orc_ctx *cx, const real_t *f, const real_t *g, int
     real_t fr[9], gr[9];
     node_state(cx, f, g, x, y, &st, fr, gr);
     orc_cell c;
-    cell_constants(cx, node_eps(cx, x, y), &c);
+    node_cell(cx, x, y, &c);
     real_t feq[9], Fi[9], geq[9], Pi[9], Qi[9];
     flow_eq(cx, &c, st.p, st.u, st.S, 1, feq);
     flow_force_terms(cx, &c, st.u, st.F, Fi);
@@ -555,11 +586,11 @@ int orc_lattice(int32_t cx_out[9], int32_t cy_out[9], double w_out[9], double va
     return 0;
 }
 
-/* derived: L, T0, dT, U, gbeta, nu, nu_e, alpha_e, A, B, K, Feps (12 values) */
-int orc_derived_values(const orc_problem *pb, double out[12]) {
+/* derived: L, T0, dT, U, gbeta, nu, nu_e, alpha_e, A, B, K, Feps, Q (13 values) */
+int orc_derived_values(const orc_problem *pb, double out[13]) {
     orc_derived d;
     int rc = orc_derive(pb, &d);
-    double v[12] = {d.L, d.T0, d.dT, d.U, d.gbeta, d.nu, d.nu_e, d.alpha_e, d.A, d.B, d.K, d.Feps};
+    double v[13] = {d.L, d.T0, d.dT, d.U, d.gbeta, d.nu, d.nu_e, d.alpha_e, d.A, d.B, d.K, d.Feps, d.Q};
     memcpy(out, v, sizeof(v));
     return rc;
 }
@@ -635,7 +666,7 @@ int orc_init(const orc_problem *pb, const real_t *T, const real_t *ux, const rea
         for (int x = 0; x < nx; ++x) {
             size_t k = (size_t)y * nx + x;
             orc_cell c;
-            cell_constants(&cx, node_eps(&cx, x, y), &c);
+            node_cell(&cx, x, y, &c);
             real_t u[2] = {ux ? ux[k] : 0.0, uy ? uy[k] : 0.0};
             real_t t = T ? T[k] : pb->T_init;
             real_t fe[9], ge[9];
@@ -777,6 +808,20 @@ int orc_residual(int64_t n, const double *ux, const double *uy, const double *T,
     }
     out[0] = du / nu_;
     out[1] = dT / nT;
+    return 0;
+}
+
+/* Stream function of a velocity field [ny][nx] (Sec. 4.3, Table 3): u_x is
+ * d psi / dy, psi vanishes on the bottom row, and each column is integrated
+ * upward with the trapezoid rule (the paper does not state its quadrature). */
+int orc_stream_function(int nx, int ny, const double *ux, double *psi) {
+    for (int x = 0; x < nx; ++x) {
+        psi[x] = 0.0;
+        for (int y = 1; y < ny; ++y) {
+            double du = 0.5 * (ux[(size_t)(y - 1) * nx + x] + ux[(size_t)y * nx + x]);
+            psi[(size_t)y * nx + x] = psi[(size_t)(y - 1) * nx + x] + du;
+        }
+    }
     return 0;
 }
 

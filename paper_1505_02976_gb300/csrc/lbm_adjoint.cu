@@ -82,7 +82,7 @@ k_adj_local(const __grid_constant__ KConst<R> k, const S* __restrict__ state, co
         const Dual<R> dex = w.wall ? Dual<R>(eps_x, j == 18 ? R(1) : R(0)) : des;
         const Dual<R> dff(thff, j == 19 ? R(1) : R(0));
         const Dual<R> dtb(thb, j == 20 ? R(1) : R(0));
-        node_update_generic(k, w, din, des, dex, dff, dtb, dout);
+        node_update_generic(k, w, din, des, dex, dff, dtb, row_ay(k, ys), row_ay(k, y), dout);
         R acc = R(0);
 #pragma unroll
         for (int q = 0; q < 17; ++q) acc += dout[q].d * l[q];

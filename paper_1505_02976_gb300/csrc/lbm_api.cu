@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 #include <new>
 #include <type_traits>
 #include <string>
@@ -94,17 +95,18 @@ lbm_status lbm_params_default(lbm_params* p) {
     p->Ra = 1e3; p->Pr = 1.0; p->Da = 1e-2; p->J = 1.0; p->eps = 0.6; p->sigma = 1.0; p->Ma = 0.1;
     p->tau_f = 1.0; p->tau_T = 1.0;
     p->Th = 1.0; p->Tc = 0.0; p->T_init = 0.5; p->rho0 = 1.0; p->Q = 0.0; p->ax = 0.0; p->ay = 0.0;
-    p->L = p->nu = p->alpha_e = p->gbeta = p->A = p->B = p->K = NAN;
+    p->L = p->nu = p->alpha_e = p->gbeta = p->A = p->B = p->K = p->T0 = NAN;
+    p->Ra_I = 0.0;
     p->T_bc[0] = 1.0; p->T_bc[1] = 0.0; p->T_bc[2] = 1.0; p->T_bc[3] = 0.0;
     return LBM_OK;
 }
 
-lbm_status lbm_derived(const lbm_params* p, double out[12]) {
+lbm_status lbm_derived(const lbm_params* p, double out[13]) {
     if (!p || !out) return LBM_ERR_ARG;
     Derived d;
     std::string why;
     lbm_status s = derive(p, &d, &why);
-    const double v[12] = {d.L, d.T0, d.dT, d.U, d.gbeta, d.nu, d.nu_e, d.alpha_e, d.A, d.B, d.K, d.Feps};
+    const double v[13] = {d.L, d.T0, d.dT, d.U, d.gbeta, d.nu, d.nu_e, d.alpha_e, d.A, d.B, d.K, d.Feps, d.Q};
     memcpy(out, v, sizeof(v));
     return s;
 }
@@ -153,7 +155,7 @@ lbm_status lbm_create(const lbm_params* p, void* stream, void* workspace, size_t
     h->k32 = make_kconst<float>(p, d, L, h->flag());
     h->diag.T0 = d.T0;
     h->diag.inv_sigma = 1.0 / p->sigma;
-    h->diag.Q = p->Q;
+    h->diag.Q = d.Q;
     h->diag.L = d.L;
     h->diag.dT = d.dT;
     for (int q = 0; q < 4; ++q) h->diag.T_bc[q] = p->T_bc[q];
@@ -272,6 +274,29 @@ lbm_status lbm_moments(lbm_handle* h, double* p, double* ux, double* uy, double*
     return LBM_OK;
 }
 
+lbm_status lbm_stream_function(lbm_handle* h, double* psi, int on_device, double range[2]) {
+    if (!h) return LBM_ERR_ARG;
+    double* F = h->fields();
+    const size_t N = h->N();
+    cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        return lbm::launch_moments(k, (const S*)h->buf(h->cur), F, F + N, F + 2 * N, F + 3 * N, h->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
+    // psi overwrites the pressure plane of the staging area
+    e = lbm::launch_stream_function(F + N, h->prm.nx, h->prm.ny, F, h->out(), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream function kernels");
+    if (psi)
+        LBM_CUDA(h, cudaMemcpyAsync(psi, F, N * sizeof(double),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream),
+                 "copy of the stream function");
+    if (range)
+        LBM_CUDA(h, cudaMemcpyAsync(range, h->out(), 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                 "copy of the stream function range");
+    if (!on_device || range) LBM_CUDA(h, cudaStreamSynchronize(h->stream), "stream function");
+    return LBM_OK;
+}
+
 lbm_status lbm_nusselt(lbm_handle* h, int side, double* nu_mean, double* nu_local) {
     if (!h) return LBM_ERR_ARG;
     if (side < 0 || side > 3 || !nu_mean) return fail(h, LBM_ERR_ARG, "bad side or null output");
@@ -352,6 +377,27 @@ lbm_status lbm_set_state(lbm_handle* h, const double* f, const double* g, int on
         LBM_CUDA(h, cudaStreamSynchronize(h->stream), "set_state");
     }
     h->nonfinite = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_force_profile(lbm_handle* h, const double* ay) {
+    if (!h) return LBM_ERR_ARG;
+    if (!ay) {
+        h->k64.ay_row = nullptr;
+        h->k32.ay_row = nullptr;
+        return LBM_OK;
+    }
+    const int ny = h->prm.ny;
+    char* area = h->ws + h->L.off_ay;
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "stream synchronise");
+    if (h->prm.precision == LBM_F64) {
+        LBM_CUDA(h, cudaMemcpy(area, ay, ny * sizeof(double), cudaMemcpyHostToDevice), "force profile");
+        h->k64.ay_row = (const double*)area;
+    } else {
+        std::vector<float> v(ay, ay + ny);
+        LBM_CUDA(h, cudaMemcpy(area, v.data(), ny * sizeof(float), cudaMemcpyHostToDevice), "force profile");
+        h->k32.ay_row = (const float*)area;
+    }
     return LBM_OK;
 }
 

@@ -180,7 +180,7 @@ lbm::BatchCavity<R> cavity_desc(const lbm_params& p, long long offset, int* flag
     c.k = make_kconst<R>(&p, d, L, flag);
     c.d.T0 = d.T0;
     c.d.inv_sigma = 1.0 / p.sigma;
-    c.d.Q = p.Q;
+    c.d.Q = d.Q;
     c.d.L = d.L;
     c.d.dT = d.dT;
     for (int q = 0; q < 4; ++q) c.d.T_bc[q] = p.T_bc[q];

@@ -80,6 +80,7 @@ struct KConst {
     R inv_sqrt_Kref;       // 1 / sqrt(K_ref)
     R p_pref_eps;          // c_s^2 / (1 - w_0)
     int da_inf, forch;
+    const R* ay_row;       // extra external acceleration a_y per row, or nullptr
     // constants of the interior fast path (see interior_update)
     R inv_rho0, half_eps_ax, half_eps, p_uF, p_uu;
     R fA_ep, fA_uu, fA_tr, fA_uF, f_cu2, f_ScS, f_cucF, f_cu, f_cF;
@@ -297,11 +298,18 @@ template <class R> __device__ __forceinline__ Dual<R> vnorm(Dual<R> sq) {
     return {r, r > R(0) ? sq.d / (R(2) * r) : R(0)};
 }
 
-// Porosity-dependent constants of one node.
+// Porosity-dependent constants of one node, and the y-component of the
+// external acceleration a at its row.
 template <class V>
 struct CellC {
-    V eps, inv_eps, e_nuK, e_FK, c0, c0sq, c1, p_pref, bcoef;
+    V eps, inv_eps, e_nuK, e_FK, c0, c0sq, c1, p_pref, bcoef, ay;
 };
+
+// a_y at row y: the uniform a_y plus the optional per-row profile.
+template <class R>
+__device__ __forceinline__ R row_ay(const KConst<R>& k, int y) {
+    return k.ay_row ? k.ay + k.ay_row[y] : k.ay;
+}
 
 template <class R>
 __device__ __forceinline__ R node_eps(const KConst<R>& k, int x, int y) {
@@ -325,6 +333,7 @@ __device__ __forceinline__ CellC<V> cell_consts(const KConst<R>& k, V eps) {
         c.c1 = V(k.c1);
         c.p_pref = V(k.p_pref);
         c.bcoef = V(k.bcoef);
+        c.ay = V(k.ay);
         return c;
     }
     c.eps = eps;
@@ -348,6 +357,7 @@ __device__ __forceinline__ CellC<V> cell_consts(const KConst<R>& k, V eps) {
     c.c1 = R(0.5) * c.e_FK;
     c.p_pref = k.p_pref_eps * c.inv_eps;
     c.bcoef = R(0.5) * (c.inv_eps - k.inv_sigma);
+    c.ay = V(k.ay);
     return c;
 }
 
@@ -379,7 +389,7 @@ __device__ __forceinline__ State<V> node_moments(const KConst<R>& k, const CellC
     const V Pxy = (f[5] + f[7]) - (f[6] + f[8]);
     // buoyancy, temporary velocity, quadratic solve
     const R Gx = k.ax;
-    const V Gy = k.gbeta * s.th + k.ay;
+    const V Gy = k.gbeta * s.th + c.ay;
     const V vx = mx * k.inv_rho0 + R(0.5) * c.eps * Gx;
     const V vy = my * k.inv_rho0 + R(0.5) * c.eps * Gy;
     const V vmag = vnorm(vx * vx + vy * vy);
@@ -486,7 +496,7 @@ __device__ __forceinline__ State<V> wall_state(const KConst<R>& k, const CellC<V
     const V umag = vnorm(b.ux * b.ux + b.uy * b.uy);
     const V drag = cb.e_nuK + cb.e_FK * umag;
     b.Fx = cb.eps * k.ax - drag * b.ux;
-    b.Fy = cb.eps * (k.gbeta * b.th + k.ay) - drag * b.uy;
+    b.Fy = cb.eps * (k.gbeta * b.th + cb.ay) - drag * b.uy;
     return b;
 }
 
@@ -531,8 +541,9 @@ __device__ __forceinline__ void eq_accumulate(const KConst<R>& k, const CellC<V>
 
 // The whole update of one node in the generic form: inputs are the 17
 // populations pulled at the source node (the node itself, or x_f for a wall
-// node), the porosity at the source and at the node, T(x_ff) - T0 and the
-// Dirichlet T_b - T0; outputs the 17 post-collision values.  Interior nodes:
+// node), the porosity at the source and at the node, T(x_ff) - T0, the
+// Dirichlet T_b - T0 and a_y at the rows of the source and of the node;
+// outputs the 17 post-collision values.  Interior nodes:
 // BGK collision (Eqs. LBEeq, TEqColli),
 //   f* = (1 - 1/tau) f + f^eq/tau + F_i.
 // Wall nodes: NEES rebuild (Eqs. NEESVel, TNEESAp) and collision with the
@@ -540,14 +551,15 @@ __device__ __forceinline__ void eq_accumulate(const KConst<R>& k, const CellC<V>
 //   f* = (1 - 1/tau)[f(x_f) - f^eq(x_f)] + f^eq(x_b) + F_i(x_b).
 template <class R, class V>
 __device__ __forceinline__ void node_update_generic(const KConst<R>& k, const WallInfo& w, const V* in,
-                                                    V eps_s, V eps_x, V thff, V thb, V* out) {
+                                                    V eps_s, V eps_x, V thff, V thb, R ay_s, R ay_x, V* out) {
     V f[9], h[9];
     f[0] = V(R(0));
 #pragma unroll
     for (int i = 1; i < 9; ++i) f[i] = in[i - 1];
 #pragma unroll
     for (int i = 0; i < 9; ++i) h[i] = in[8 + i];
-    const CellC<V> cs = cell_consts(k, eps_s);
+    CellC<V> cs = cell_consts(k, eps_s);
+    cs.ay = V(ay_s);
     const State<V> s = node_moments(k, cs, f, h);
 #pragma unroll
     for (int q = 0; q < 8; ++q) out[q] = k.omf * in[q];
@@ -558,7 +570,8 @@ __device__ __forceinline__ void node_update_generic(const KConst<R>& k, const Wa
         return;
     }
     eq_accumulate(k, cs, s, -k.omf, R(0), -k.omT, R(0), out);
-    const CellC<V> cb = cell_consts(k, eps_x);
+    CellC<V> cb = cell_consts(k, eps_x);
+    cb.ay = V(ay_x);
     const State<V> b = wall_state(k, cb, w, s, thff, thb);
     eq_accumulate(k, cb, b, R(1), R(1), R(1), R(1), out);
 }
@@ -626,7 +639,7 @@ __device__ __forceinline__ void interior_update(const KConst<R>& k, const S* __r
     const R my = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
     const R Pxx = a13 + d58, Pyy = a24 + d58;
     const R Pxy = (f[5] + f[7]) - (f[6] + f[8]);
-    const R Gy = k.gbeta * th + k.ay;
+    const R Gy = k.gbeta * th + row_ay(k, y);
     const R vx = mx * k.inv_rho0 + k.half_eps_ax;
     const R vy = my * k.inv_rho0 + k.half_eps * Gy;
     const R vmag = sqrt(vx * vx + vy * vy);

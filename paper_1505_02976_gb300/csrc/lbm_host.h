@@ -18,7 +18,7 @@ constexpr double kW0 = 4.0 / 9.0;
 constexpr int NPLANES_HOST = lbm::NPLANES;
 
 struct Derived {
-    double L, T0, dT, U, gbeta, nu, nu_e, alpha_e, A, B, K, Feps;
+    double L, T0, dT, U, gbeta, nu, nu_e, alpha_e, A, B, K, Feps, Q;
 };
 
 inline bool isnan_(double v) { return v != v; }
@@ -27,7 +27,7 @@ inline bool isnan_(double v) { return v != v; }
 // Eq. Therdiff, Appendix A): see the table in include/lbm.h.
 inline lbm_status derive(const lbm_params* p, Derived* d, std::string* why) {
     d->L = isnan_(p->L) ? double(p->nx - 1) : p->L;
-    d->T0 = 0.5 * (p->Th + p->Tc);
+    d->T0 = isnan_(p->T0) ? 0.5 * (p->Th + p->Tc) : p->T0;
     d->dT = p->Th - p->Tc;
     d->U = p->Ma * sqrt(kCs2);
     d->gbeta = isnan_(p->gbeta) ? d->U * d->U / (d->dT * d->L) : p->gbeta;
@@ -42,6 +42,7 @@ inline lbm_status derive(const lbm_params* p, Derived* d, std::string* why) {
     d->B = isnan_(p->B) ? p->tau_T - 0.5 - d->alpha_e / (p->sigma * kCs2) : p->B;
     d->K = p->da_infinite ? INFINITY : (isnan_(p->K) ? p->Da * d->L * d->L : p->K);
     d->Feps = p->forchheimer ? 1.75 / sqrt(150.0 * p->eps * p->eps * p->eps) : 0.0;
+    d->Q = isnan_(p->Q) ? p->Ra_I * d->alpha_e * d->dT / (p->Ra * d->L * d->L) : p->Q;
     auto bad = [&](const char* m) {
         if (why) *why = m;
         return LBM_ERR_PARAM_RANGE;
@@ -51,8 +52,9 @@ inline lbm_status derive(const lbm_params* p, Derived* d, std::string* why) {
     if (!(d->A < p->tau_f - 0.5)) return bad("A must be below tau_f - 1/2 (positive viscosity)");
     if (!(d->B < p->tau_T - 0.5)) return bad("B must be below tau_T - 1/2 (positive diffusivity)");
     if (!(p->sigma > 0.0 && p->rho0 > 0.0)) return bad("sigma and rho0 must be positive");
-    if (!(isfinite(d->gbeta) && isfinite(d->nu) && isfinite(d->alpha_e) && isfinite(d->T0)))
-        return bad("derived constants are not finite (check Ra, Pr, Ma, Th - Tc)");
+    if (!(isfinite(d->gbeta) && isfinite(d->nu) && isfinite(d->alpha_e) && isfinite(d->T0) &&
+          isfinite(d->Q)))
+        return bad("derived constants are not finite (check Ra, Ra_I, Pr, Ma, Th - Tc)");
     return LBM_OK;
 }
 
@@ -92,7 +94,7 @@ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 struct Layout {
     int pitch;
     size_t plane_elems, buf_bytes;
-    size_t off_buf[2], off_fields, off_snap, off_nu, off_partial, off_eps, off_out, off_flag, total;
+    size_t off_buf[2], off_fields, off_snap, off_nu, off_partial, off_eps, off_ay, off_out, off_flag, total;
 };
 
 inline Layout layout(const lbm_params* p) {
@@ -111,6 +113,7 @@ inline Layout layout(const lbm_params* p) {
     L.off_nu = o; o += align256((size_t)(p->nx > p->ny ? p->nx : p->ny) * sizeof(double));
     L.off_partial = o; o += align256((size_t)lbm::residual_blocks(p->nx, p->ny) * 4 * sizeof(double));
     L.off_eps = o; o += align256(N * sizeof(double));
+    L.off_ay = o; o += align256((size_t)p->ny * sizeof(double));
     L.off_out = o; o += 256;
     L.off_flag = o; o += 256;
     L.total = o;
@@ -147,7 +150,7 @@ inline lbm::KConst<R> make_kconst(const lbm_params* p, const Derived& d, const L
     k.gbeta = R(d.gbeta);
     k.ax = R(p->ax);
     k.ay = R(p->ay);
-    k.Q = R(p->Q);
+    k.Q = R(d.Q);
     k.e_nuK = R(eps * nuK);
     k.e_FK = R(eps * FK);
     k.c0 = R(c0);
@@ -189,17 +192,17 @@ inline lbm::KConst<R> make_kconst(const lbm_params* p, const Derived& d, const L
     k.h_sig = R(itT * p->sigma);
     k.h_uu = R(itT * 1.5 * ie);
     k.h_pT = R(itT * 3.0 / rho0);
-    k.h_kQ = R(kT * p->Q);
+    k.h_kQ = R(kT * d.Q);
     k.h_cu2 = R(itT * 4.5 * ie);
     k.h_u3 = R(3.0 * itT);
     k.h_ug = R(6.0 * kT * bc);
-    k.h_uQ = R(3.0 * kT * p->Q / p->sigma);
+    k.h_uQ = R(3.0 * kT * d.Q / p->sigma);
     k.h_g = R(itT * p->sigma * d.B);
     k.h_W = R(3.0 * kT);
     k.h0_sig = R(itT * kW0 * p->sigma);
     k.h0_uu = R(itT * kW0 * 1.5 * ie);
     k.h0_pT = R(itT * (5.0 / 3.0) / rho0);
-    k.h0_kQ = R(kW0 * kT * p->Q);
+    k.h0_kQ = R(kW0 * kT * d.Q);
     // porosity field support (the field pointer is set by lbm_set_fields)
     k.eps_field = nullptr;
     k.kc_inv_ref = R(eps < 1.0 ? (1.0 - eps) * (1.0 - eps) / (eps * eps * eps) : 0.0);
@@ -208,6 +211,7 @@ inline lbm::KConst<R> make_kconst(const lbm_params* p, const Derived& d, const L
     k.p_pref_eps = R(kCs2 / (1.0 - kW0));
     k.da_inf = p->da_infinite ? 1 : 0;
     k.forch = p->forchheimer ? 1 : 0;
+    k.ay_row = nullptr;
     return k;
 }
 

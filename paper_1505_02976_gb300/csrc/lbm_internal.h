@@ -56,6 +56,11 @@ template <class R, class S>
 cudaError_t launch_totals(const KConst<R>& k, const S* src, double sT0, double* partial, double* out,
                           cudaStream_t st);
 
+// Stream function psi [ny][nx] from u_x [ny][nx] (psi = 0 along y = 0,
+// trapezoid rule up each column); range[0..1] = min, max of psi.
+cudaError_t launch_stream_function(const double* ux, int nx, int ny, double* psi, double* range,
+                                   cudaStream_t st);
+
 // out[i] = R(in[i]) for i < n.
 template <class R>
 cudaError_t launch_convert(const double* in, R* out, long long n, cudaStream_t st);

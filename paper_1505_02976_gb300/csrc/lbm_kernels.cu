@@ -35,12 +35,16 @@ __device__ __forceinline__ State<R> node_state_at(const KConst<R>& k, const S* _
     const int xs = w.wall ? w.xs : x, ys = w.wall ? w.ys : y;
     Pops<R> P;
     pull(k, src, xs, ys, P);
-    const State<R> s = node_moments(k, cell_consts(k, node_eps(k, xs, ys)), P.f, P.h);
+    CellC<R> cs = cell_consts(k, node_eps(k, xs, ys));
+    cs.ay = row_ay(k, ys);
+    const State<R> s = node_moments(k, cs, P.f, P.h);
     if (!w.wall) return s;
     R thff = R(0);
     if (w.tside < 0) thff = (pull_hsum<R, R, S>(k, src, w.xff, w.yff) + R(0.5) * k.Q) * k.inv_sigma;
     const R thb = w.tside >= 0 ? k.T_bc[w.tside] - k.T0 : R(0);
-    return wall_state(k, cell_consts(k, node_eps(k, x, y)), w, s, thff, thb);
+    CellC<R> cb = cell_consts(k, node_eps(k, x, y));
+    cb.ay = row_ay(k, y);
+    return wall_state(k, cb, w, s, thff, thb);
 }
 
 // Wall node of one step: the generic update of its x_f neighbour's pulled
@@ -61,7 +65,8 @@ __device__ __noinline__ void wall_update(const KConst<R>& k, const S* __restrict
     R thff = R(0);
     if (w.tside < 0) thff = (pull_hsum<R, R, S>(k, src, w.xff, w.yff) + R(0.5) * k.Q) * k.inv_sigma;
     const R thb = w.tside >= 0 ? k.T_bc[w.tside] - k.T0 : R(0);
-    node_update_generic(k, w, in, node_eps(k, w.xs, w.ys), node_eps(k, x, y), thff, thb, out);
+    node_update_generic(k, w, in, node_eps(k, w.xs, w.ys), node_eps(k, x, y), thff, thb, row_ay(k, w.ys),
+                        row_ay(k, y), out);
     if (!isfinite(out[0] + out[8])) atomicOr(k.flag, 1);
     R fo[9], ho[9];
 #pragma unroll
@@ -302,6 +307,49 @@ __global__ void k_reduce4(const double* __restrict__ partial, long long nb, doub
     }
 }
 
+// Stream function up each column x: psi(x, 0) = 0 and
+// psi(x, y) = psi(x, y - 1) + (u_x(x, y - 1) + u_x(x, y)) / 2, the trapezoid
+// rule for u_x = d psi / dy.  One thread per column; rows are coalesced.
+__global__ void k_stream_function(const double* __restrict__ ux, int nx, int ny, double* __restrict__ psi) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    double s = 0.0;
+    psi[x] = 0.0;
+    for (int y = 1; y < ny; ++y) {
+        s = s + 0.5 * (ux[(long long)(y - 1) * nx + x] + ux[(long long)y * nx + x]);
+        psi[(long long)y * nx + x] = s;
+    }
+}
+
+// out[0] = min, out[1] = max of v[0 .. n-1] (one block; order-independent).
+__global__ void k_minmax(const double* __restrict__ v, long long n, double* __restrict__ out) {
+    __shared__ double lo_s[kReduceBlock / 32], hi_s[kReduceBlock / 32];
+    double lo = INFINITY, hi = -INFINITY;
+    for (long long i = threadIdx.x; i < n; i += kReduceBlock) {
+        lo = fmin(lo, v[i]);
+        hi = fmax(hi, v[i]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        lo_s[wid] = lo;
+        hi_s[wid] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < kReduceBlock / 32; ++i) {
+            lo = fmin(lo, lo_s[i]);
+            hi = fmax(hi, hi_s[i]);
+        }
+        out[0] = lo;
+        out[1] = hi;
+    }
+}
+
 template <class R>
 __global__ void k_convert(const double* __restrict__ in, R* __restrict__ out, long long n) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -319,6 +367,15 @@ template cudaError_t launch_convert<double>(const double*, double*, long long, c
 template cudaError_t launch_convert<float>(const double*, float*, long long, cudaStream_t);
 
 static dim3 row_grid(int nx, int ny, int bx) { return dim3((unsigned)((nx + bx - 1) / bx), (unsigned)ny); }
+
+cudaError_t launch_stream_function(const double* ux, int nx, int ny, double* psi, double* range,
+                                   cudaStream_t st) {
+    k_stream_function<<<(nx + 127) / 128, 128, 0, st>>>(ux, nx, ny, psi);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_minmax<<<1, kReduceBlock, 0, st>>>(psi, (long long)nx * ny, range);
+    return cudaGetLastError();
+}
 
 long long residual_blocks(int nx, int ny) {
     return (long long)((nx + kResBlock - 1) / kResBlock) * ny;

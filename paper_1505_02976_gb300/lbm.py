@@ -30,7 +30,8 @@ EXPORTED = ("lbm_params_default", "lbm_derived", "lbm_workspace_size", "lbm_crea
             "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_set_fields", "lbm_batch_step",
             "lbm_batch_autotune", "lbm_batch_set_launch", "lbm_batch_sync", "lbm_batch_nusselt",
             "lbm_batch_moments", "lbm_batch_steps_done", "lbm_batch_kernel_launches",
-            "lbm_adjoint", "lbm_totals", "lbm_checkpoint")
+            "lbm_adjoint", "lbm_totals", "lbm_checkpoint", "lbm_set_force_profile",
+            "lbm_stream_function")
 BATCH_MODE = {"fused": 0, "graph": 1, "per_case": 2}
 
 
@@ -53,6 +54,7 @@ class lbm_params(C.Structure):
         ("L", C.c_double), ("nu", C.c_double), ("alpha_e", C.c_double), ("gbeta", C.c_double),
         ("A", C.c_double), ("B", C.c_double), ("K", C.c_double),
         ("T_bc", C.c_double * 4), ("u_bc", (C.c_double * 2) * 4),
+        ("T0", C.c_double), ("Ra_I", C.c_double),
     ]
 
 
@@ -96,6 +98,8 @@ def load(build_if_missing: bool = True):
     L.lbm_adjoint.argtypes = [H, C.c_int64, C.c_int64, C.c_int, dp, C.c_void_p, C.c_void_p]
     L.lbm_totals.argtypes = [H, dp, dp]
     L.lbm_checkpoint.argtypes = [H, C.c_char_p, C.c_int]
+    L.lbm_set_force_profile.argtypes = [H, C.c_void_p]
+    L.lbm_stream_function.argtypes = [H, C.c_void_p, C.c_int, dp]
     B = C.c_void_p
     L.lbm_batch_workspace_size.argtypes = [P, C.c_int32, C.POINTER(C.c_size_t)]
     L.lbm_batch_create.argtypes = [P, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(B)]
@@ -138,9 +142,9 @@ def params_from_problem(p: dict, precision: str = "f32") -> lbm_params:
     s.precision = PRECISION[precision]
     s.reserved = 0
     for name in ("Ra", "Pr", "Da", "J", "eps", "sigma", "Ma", "tau_f", "tau_T", "Th", "Tc",
-                 "T_init", "rho0", "Q", "ax", "ay"):
+                 "T_init", "rho0", "Q", "ax", "ay", "Ra_I"):
         setattr(s, name, float(p[name]))
-    for name in ("L", "nu", "alpha_e", "gbeta", "A", "B", "K"):
+    for name in ("L", "nu", "alpha_e", "gbeta", "A", "B", "K", "T0"):
         setattr(s, name, _nan(p[name]))
     for k in range(4):
         s.T_bc[k] = float(p["T_bc"][k])
@@ -155,11 +159,11 @@ def _check(status: int, handle=None):
         raise LbmError(status, msg.decode() if msg else "")
 
 
-DERIVED_KEYS = ("L", "T0", "dT", "U", "gbeta", "nu", "nu_e", "alpha_e", "A", "B", "K", "Feps")
+DERIVED_KEYS = ("L", "T0", "dT", "U", "gbeta", "nu", "nu_e", "alpha_e", "A", "B", "K", "Feps", "Q")
 
 
 def lbm_derived(p: dict) -> dict:
-    out = (C.c_double * 12)()
+    out = (C.c_double * 13)()
     _check(load().lbm_derived(C.byref(params_from_problem(p)), out))
     return dict(zip(DERIVED_KEYS, list(out)))
 
@@ -270,6 +274,18 @@ class Lattice:
         ru, rT = C.c_double(), C.c_double()
         _check(self.lib.lbm_residual(self.h, C.byref(ru), C.byref(rT)), self.h)
         return ru.value, rT.value
+
+    def stream_function(self):
+        """(psi [ny][nx], (min psi, max psi)): u_x = d psi/dy, psi = 0 on row 0."""
+        psi = np.empty((self.ny, self.nx))
+        rng = np.empty(2)
+        _check(self.lib.lbm_stream_function(self.h, _ptr(psi), 0, _ptr(rng)), self.h)
+        return psi, (float(rng[0]), float(rng[1]))
+
+    def set_force_profile(self, ay=None):
+        """Per-row external acceleration a_y(y) (None removes it)."""
+        a = None if ay is None else np.ascontiguousarray(ay, np.float64)
+        _check(self.lib.lbm_set_force_profile(self.h, _ptr(a)), self.h)
 
     def save(self, path: str):
         _check(self.lib.lbm_checkpoint(self.h, os.fsencode(path), 1), self.h)

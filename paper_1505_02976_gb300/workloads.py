@@ -34,7 +34,7 @@ _DEFAULTS = dict(
     Ra=1e3, Pr=1.0, Da=1e-2, J=1.0, eps=0.6, sigma=1.0, Ma=0.1,
     tau_f=1.0, tau_T=1.0,
     Th=1.0, Tc=0.0, T_init=0.5, rho0=1.0, Q=0.0, ax=0.0, ay=0.0,
-    L=NAN, nu=NAN, alpha_e=NAN, gbeta=NAN, A=NAN, B=NAN, K=NAN,
+    L=NAN, nu=NAN, alpha_e=NAN, gbeta=NAN, A=NAN, B=NAN, K=NAN, T0=NAN, Ra_I=0.0,
     T_bc=None, u_bc=((0.0, 0.0), (0.0, 0.0), (0.0, 0.0), (0.0, 0.0)),
 )
 
@@ -66,6 +66,34 @@ def cavity(n: int, Ra: float, Da: float, eps: float, Pr: float = 1.0, ny: int | 
     (Tc = 0), adiabatic top and bottom, no slip everywhere, u = 0 and T = 0.5
     at t = 0."""
     return problem(nx=n, ny=ny or n, Ra=Ra, Da=Da, eps=eps, Pr=Pr, **kw)
+
+
+def clear_fluid_cavity(n: int, Ra: float, Pr: float = 0.71, **kw) -> dict:
+    """The Sec. 4.2 cavity in the clear-fluid limit of Table 1: eps = 0.9999,
+    Da = 1e8 (n x n nodes; the paper's "N x N grid" is n = N + 1 here)."""
+    return cavity(n, Ra, 1e8, 0.9999, Pr=Pr, **kw)
+
+
+def heat_generating_cavity(n: int, Da: float, Ra_I: float = 6.4e5, Pr: float = 1.0,
+                           eps: float = 1.0, dT: float = 10.0, **kw) -> dict:
+    """Sec. 4.3 (Table 3): a heat-generating fluid in a porous cavity whose
+    four no-slip walls are held at T_c = 0.  dT = Q L^2 / alpha_e = 10 sets the
+    temperature scale (carried here as Th - Tc; no wall is at Th), T0 = T_c,
+    Ra = 0 so that Ra_I sets the viscosity scale (the Ra slot carries Ra_I),
+    Brinkman-extended Darcy flow (F_eps = 0); Da = inf gives the clear fluid.
+    Q is left to the derivation Q = Ra_I alpha_e dT / (Ra L^2) = alpha_e dT / L^2.
+    The fluid starts at rest at T_c."""
+    inf = math.isinf(Da)
+    return problem(nx=n, ny=n, bc=("dirichlet",) * 4, Th=dT, Tc=0.0, T0=0.0, T_init=0.0,
+                   T_bc=(0.0, 0.0, 0.0, 0.0), Ra=Ra_I, Ra_I=Ra_I, Q=NAN, Pr=Pr, eps=eps,
+                   Da=1.0 if inf else Da, da_infinite=int(inf), forchheimer=0, **kw)
+
+
+def heated_cavity_with_source(n: int, Ra: float, Ra_I: float, Da: float, eps: float = 0.4,
+                              Pr: float = 0.7, **kw) -> dict:
+    """Sec. 4.4 (Table 4): the sidewall-heated cavity of Sec. 4.2 with a
+    uniform internal heat source Q = Ra_I alpha_e (Th - Tc) / (Ra L^2)."""
+    return cavity(n, Ra, Da, eps, Pr=Pr, Q=NAN, Ra_I=Ra_I, **kw)
 
 
 def poiseuille(nx: int = 8, ny: int = 64, G: float = 1e-5, eps: float = 0.5,

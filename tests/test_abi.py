@@ -45,7 +45,7 @@ def test_params_struct_layout_matches_header():
     assert (p.Ra, p.Da, p.eps, p.Pr, p.Ma) == (1e3, 1e-2, 0.6, 1.0, 0.1)
     assert math.isnan(p.A) and math.isnan(p.K)
     assert list(p.T_bc) == [1.0, 0.0, 1.0, 0.0]
-    assert C.sizeof(lbm.lbm_params) == 10 * 4 + 8 * (7 + 2 + 7 + 7 + 4 + 8)
+    assert C.sizeof(lbm.lbm_params) == 10 * 4 + 8 * (7 + 2 + 7 + 7 + 4 + 8 + 2)
 
 
 PROBLEMS = [
