@@ -33,8 +33,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="cavity2048_fp32", n=2048, Ra=1e6, Da=1e-4, eps=0.4, Pr=1.0, precision="f32")
-BYTES_PER_CELL = {"f64": 17 * 8 * 2, "f32": 17 * 4 * 2, "f16": 17 * 2 * 2}
+WORKLOAD = dict(name="cavity2048_fp32", n=2048, Ra=1e6, Da=1e-4, eps=0.4, Pr=1.0, precision="f32",
+                state="populations")
+BYTES_PER_CELL = {"f64": 17 * 8 * 2, "f32": 17 * 4 * 2, "f16": 17 * 2 * 2,
+                  "f32/moments": 9 * 4 * 2, "f64/moments": 9 * 8 * 2}
 METRIC = "coupled flow+thermal MLUPS and % HBM roofline at 1 GB300 (plain FP32 fused step)"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_f32_2048_traffic.json")
 KERNEL_SOURCES = ("paper_1505_02976_gb300/csrc/lbm_device.cuh", "paper_1505_02976_gb300/csrc/lbm_kernels.cu")
@@ -235,21 +237,25 @@ def variant_lines(device, local, warmup: int, steps: int) -> dict:
     from paper_1505_02976_gb300 import workloads as W
     out = {}
     peak, _ = measured_peak_gbs()
-    for name, prec, p in (
-            ("cavity8192_fp16", "f16", W.config_problem(W.CONFIG_FP16_CAVITY)),
-            ("cavity2048_fp64", "f64", W.cavity(WORKLOAD["n"], WORKLOAD["Ra"], WORKLOAD["Da"], WORKLOAD["eps"]))):
+    bench_p = W.cavity(WORKLOAD["n"], WORKLOAD["Ra"], WORKLOAD["Da"], WORKLOAD["eps"])
+    other = "populations" if WORKLOAD["state"] == "moments" else "moments"
+    for name, prec, p, state in (
+            ("cavity8192_fp16", "f16", W.config_problem(W.CONFIG_FP16_CAVITY), "populations"),
+            ("cavity2048_fp64", "f64", bench_p, "populations"),
+            (f"cavity2048_fp32_{other}", "f32", bench_p, other)):
         stream = torch.cuda.Stream(device)
-        lat = lbm.Lattice(p, prec, device=local, stream=stream)
+        lat = lbm.Lattice(p, prec, device=local, stream=stream, state=state)
+        key = prec if state == "populations" else f"{prec}/moments"
         lat.step(warmup)
         lat.sync()
         kernel, loop = time_steps(lat, stream, steps)
         lat.sync()
         cells = p["nx"] * p["ny"]
-        gbs = BYTES_PER_CELL[prec] * cells / kernel / 1e9
-        out[name] = {"value": cells * steps / loop / 1e6, "unit": "MLUPS", "dtype": prec,
+        gbs = BYTES_PER_CELL[key] * cells / kernel / 1e9
+        out[name] = {"value": cells * steps / loop / 1e6, "unit": "MLUPS", "dtype": prec, "state": state,
                      "ms_per_step": 1e3 * loop / steps, "kernel_ms": 1e3 * kernel,
                      "hbm_gbs": gbs, "hbm_frac": gbs / peak,
-                     "bytes_per_node": BYTES_PER_CELL[prec]}
+                     "bytes_per_node": BYTES_PER_CELL[key]}
         lat.close()
         del lat
         torch.cuda.empty_cache()
@@ -347,7 +353,7 @@ def run_ours(args):
     p = W.cavity(n, WORKLOAD["Ra"], WORKLOAD["Da"], WORKLOAD["eps"], Pr=WORKLOAD["Pr"])
     stream = torch.cuda.Stream(device)
     with torch.cuda.stream(stream):
-        lat = lbm.Lattice(p, prec, device=local, stream=stream)
+        lat = lbm.Lattice(p, prec, device=local, stream=stream, state=WORKLOAD["state"])
     cells = n * n
 
     # warm-up
@@ -403,7 +409,8 @@ def run_ours(args):
     d2h = 8 + n * 8
 
     peak, peak_kind = measured_peak_gbs()
-    algo_bytes = BYTES_PER_CELL[prec] * cells
+    key = prec if WORKLOAD["state"] == "populations" else f"{prec}/moments"
+    algo_bytes = BYTES_PER_CELL[key] * cells
     achieved = algo_bytes / kernel_s / 1e9
     traffic = ncu_traffic_per_launch()
 
@@ -419,7 +426,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "nx": n, "ny": n, "Ra": WORKLOAD["Ra"],
                        "Da": WORKLOAD["Da"], "eps": WORKLOAD["eps"], "Pr": WORKLOAD["Pr"],
-                       "storage": prec, "replicas": world,
+                       "storage": prec, "state": WORKLOAD["state"], "replicas": world,
                        "l2": "inputs larger than L2: 285 MB of populations read and 285 MB "
                              "written per step (L2 129 MB), no flush needed"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -451,11 +458,14 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP16 / FP64 comparison lines")
+    ap.add_argument("--state", choices=("populations", "moments"), default=WORKLOAD["state"],
+                    help="storage of the timed lattice (moments: the tau = 1 moment state)")
     ap.add_argument("--n", type=int, default=None,
                     help="lattice size override (profiling captures only; changes the workload)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    WORKLOAD["state"] = args.state
     if args.n:
         WORKLOAD["n"] = args.n
         WORKLOAD["name"] = f"cavity{args.n}_{WORKLOAD['precision']}"

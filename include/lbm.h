@@ -94,7 +94,7 @@ typedef struct {
     int32_t forchheimer;     /* 1: Ergun F_eps, 0: no quadratic drag */
     int32_t da_infinite;     /* 1: K = infinity (no Darcy/Forchheimer drag) */
     int32_t precision;       /* lbm_precision */
-    int32_t reserved;        /* must be 0 */
+    int32_t moment_state;    /* 1: store the moment state (tau_f = tau_T = 1; see below) */
     double Ra, Pr, Da, J, eps, sigma, Ma;
     double tau_f, tau_T;
     double Th, Tc, T_init, rho0, Q, ax, ay;
@@ -104,6 +104,18 @@ typedef struct {
     double T0;               /* NaN = derive */
     double Ra_I;             /* internal Rayleigh number (used when Q is NaN) */
 } lbm_params;
+
+/* Moment state (moment_state = 1).  At tau_f = tau_T = 1 the collision
+ * leaves f* = f^eq + F_i and g* = g^eq + P_i + Q_i (Eqs. LBEeq, TEqColli),
+ * functions of the nine numbers (p, u, S, T, grad T) that a step computes
+ * for every node (wall nodes: their boundary state, Sec. 3.4).  The handle
+ * then stores those nine moments per node instead of the 17 populations and
+ * each step rebuilds the populations in on-chip memory; the results are the
+ * same as with population storage up to rounding.  Requires tau_f = tau_T = 1
+ * and LBM_F32 or LBM_F64 (else LBM_ERR_ARG).  lbm_set_state and lbm_adjoint
+ * need population storage and return LBM_ERR_ARG on such a handle; every
+ * other call behaves as with populations (lbm_get_state returns the
+ * post-collision populations the moments define). */
 
 /* Fill p with the paper's defaults (Sec. 4): the 32 x 32 porous cavity,
  * hot W wall T = 1, cold E wall T = 0, adiabatic S and N, no slip, rho0 = 1,

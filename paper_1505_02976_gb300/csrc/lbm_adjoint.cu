@@ -362,6 +362,8 @@ extern "C" lbm_status lbm_adjoint(lbm_handle* h, int64_t n_steps, int64_t segmen
         return lbm_handle_fail(h, LBM_ERR_ARG, "bad step count, segment, side or null loss");
     if (h->prm.precision == LBM_F16)
         return lbm_handle_fail(h, LBM_ERR_ARG, "the adjoint runs on FP64 or FP32 storage");
+    if (h->moments_kind())
+        return lbm_handle_fail(h, LBM_ERR_ARG, "the adjoint runs on population storage, not on a moment state");
     if (h->nonfinite) return lbm_handle_fail(h, LBM_ERR_NONFINITE, "non-finite velocity or temperature");
     const bool field = h->prm.precision == LBM_F64 ? h->k64.eps_field != nullptr : h->k32.eps_field != nullptr;
     if (dloss_deps && !field)

@@ -68,7 +68,28 @@ lbm_status copy_in(lbm_handle* h, double* dst, const double* src, int on_device)
     return LBM_OK;
 }
 
+// Moment state: bring the expansion buffer up to date with the moments (a
+// no-op with population storage, or when nothing changed since the last one).
+lbm_status ensure_pops(lbm_handle* h) {
+    if (!h->moments_kind() || h->pops_valid) return LBM_OK;
+    cudaError_t e = h->prm.precision == LBM_F64
+                        ? lbm::launch_expand_m(h->k64, (const double*)h->mom(h->mcur), (double*)h->buf(0),
+                                               h->msources, h->stream)
+                        : lbm::launch_expand_m(h->k32, (const float*)h->mom(h->mcur), (float*)h->buf(0),
+                                               h->msources, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moment expansion");
+    h->pops_valid = true;
+    return LBM_OK;
+}
+
+#define LBM_POPS(h)                                  \
+    do {                                             \
+        lbm_status s_ = ensure_pops(h);              \
+        if (s_ != LBM_OK) return s_;                 \
+    } while (0)
+
 lbm_status reset_snapshot(lbm_handle* h) {
+    LBM_POPS(h);
     cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         return lbm::launch_residual(k, (const S*)h->buf(h->cur), h->snap(), h->partial(), h->out(), h->stream);
@@ -151,8 +172,15 @@ lbm_status lbm_create(const lbm_params* p, void* stream, void* workspace, size_t
     h->cur = 0;
     h->steps = h->launches = 0;
     h->nonfinite = false;
+    h->mcur = 0;
+    h->msources = false;
+    h->pops_valid = false;
     h->k64 = make_kconst<double>(p, d, L, h->flag());
     h->k32 = make_kconst<float>(p, d, L, h->flag());
+    h->msegments = 1;
+    if (p->moment_state)
+        h->msegments = p->precision == LBM_F64 ? lbm::moment_segments_default(h->k64)
+                                               : lbm::moment_segments_default(h->k32);
     h->diag.T0 = d.T0;
     h->diag.inv_sigma = 1.0 / p->sigma;
     h->diag.Q = d.Q;
@@ -215,10 +243,20 @@ lbm_status lbm_set_fields(lbm_handle* h, const double* T, const double* ux, cons
     if (ux) { if ((s = copy_in(h, F + N, ux, on_device)) != LBM_OK) return s; dux = F + N; }
     if (uy) { if ((s = copy_in(h, F + 2 * N, uy, on_device)) != LBM_OK) return s; duy = F + 2 * N; }
     h->cur = 0;
-    cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
-        using S = std::remove_pointer_t<decltype(tag)>;
-        return lbm::launch_init(k, (S*)h->buf(0), dT, dux, duy, h->prm.T_init, h->stream);
-    });
+    cudaError_t e;
+    if (h->moments_kind()) {
+        h->mcur = 0;
+        h->msources = false;
+        h->pops_valid = false;
+        e = h->prm.precision == LBM_F64
+                ? lbm::launch_init_m(h->k64, (double*)h->mom(0), dT, dux, duy, h->prm.T_init, h->stream)
+                : lbm::launch_init_m(h->k32, (float*)h->mom(0), dT, dux, duy, h->prm.T_init, h->stream);
+    } else {
+        e = dispatch(h, [&](auto& k, auto* tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            return lbm::launch_init(k, (S*)h->buf(0), dT, dux, duy, h->prm.T_init, h->stream);
+        });
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "init kernel");
     LBM_CUDA(h, cudaMemsetAsync(h->flag(), 0, sizeof(int), h->stream), "flag reset");
     if ((s = reset_snapshot(h)) != LBM_OK) return s;
@@ -231,6 +269,23 @@ lbm_status lbm_set_fields(lbm_handle* h, const double* T, const double* ux, cons
 lbm_status lbm_step(lbm_handle* h, int64_t n) {
     if (!h || n < 0) return h ? fail(h, LBM_ERR_ARG, "negative step count") : LBM_ERR_ARG;
     if (h->nonfinite) return fail(h, LBM_ERR_NONFINITE, "non-finite velocity or temperature");
+    if (h->moments_kind()) {
+        for (int64_t i = 0; i < n; ++i) {
+            const int src = h->mcur, dst = 1 - h->mcur;
+            cudaError_t e = h->prm.precision == LBM_F64
+                                ? lbm::launch_step_m(h->k64, (const double*)h->mom(src), (double*)h->mom(dst),
+                                                     h->msources, h->msegments, h->stream)
+                                : lbm::launch_step_m(h->k32, (const float*)h->mom(src), (float*)h->mom(dst),
+                                                     h->msources, h->msegments, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "moment step kernel");
+            h->mcur = dst;
+            h->msources = true;
+            h->pops_valid = false;
+            ++h->steps;
+            ++h->launches;
+        }
+        return LBM_OK;
+    }
     for (int64_t i = 0; i < n; ++i) {
         const int src = h->cur, dst = 1 - h->cur;
         cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
@@ -257,6 +312,7 @@ lbm_status lbm_sync(lbm_handle* h) {
 
 lbm_status lbm_moments(lbm_handle* h, double* p, double* ux, double* uy, double* T, int on_device) {
     if (!h) return LBM_ERR_ARG;
+    LBM_POPS(h);
     double* F = h->fields();
     const size_t N = h->N();
     cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
@@ -276,6 +332,7 @@ lbm_status lbm_moments(lbm_handle* h, double* p, double* ux, double* uy, double*
 
 lbm_status lbm_stream_function(lbm_handle* h, double* psi, int on_device, double range[2]) {
     if (!h) return LBM_ERR_ARG;
+    LBM_POPS(h);
     double* F = h->fields();
     const size_t N = h->N();
     cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
@@ -303,6 +360,7 @@ lbm_status lbm_nusselt(lbm_handle* h, int side, double* nu_mean, double* nu_loca
     const int n = side <= 1 ? h->prm.ny : h->prm.nx;
     const int across = side <= 1 ? h->prm.nx : h->prm.ny;
     if (across < 3) return fail(h, LBM_ERR_ARG, "the one-sided difference needs 3 nodes");
+    LBM_POPS(h);
     cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         return lbm::launch_nusselt(k, h->diag, (const S*)h->buf(h->cur), side, h->nu(), h->out(), h->stream);
@@ -330,6 +388,7 @@ lbm_status lbm_residual(lbm_handle* h, double* res_u, double* res_T) {
 
 lbm_status lbm_get_state(lbm_handle* h, double* f, double* g, int on_device) {
     if (!h || !f || !g) return h ? fail(h, LBM_ERR_ARG, "null output") : LBM_ERR_ARG;
+    LBM_POPS(h);
     const size_t bytes = 9 * h->N() * sizeof(double);
     double* df = f;
     double* dg = g;
@@ -355,6 +414,8 @@ lbm_status lbm_get_state(lbm_handle* h, double* f, double* g, int on_device) {
 
 lbm_status lbm_set_state(lbm_handle* h, const double* f, const double* g, int on_device) {
     if (!h || !f || !g) return h ? fail(h, LBM_ERR_ARG, "null input") : LBM_ERR_ARG;
+    if (h->moments_kind())
+        return fail(h, LBM_ERR_ARG, "set_state needs population storage (a moment state holds no arbitrary populations)");
     const size_t bytes = 9 * h->N() * sizeof(double);
     const double* df = f;
     const double* dg = g;
@@ -385,9 +446,11 @@ lbm_status lbm_set_force_profile(lbm_handle* h, const double* ay) {
     if (!ay) {
         h->k64.ay_row = nullptr;
         h->k32.ay_row = nullptr;
+        h->pops_valid = false;
         return LBM_OK;
     }
     const int ny = h->prm.ny;
+    h->pops_valid = false;
     char* area = h->ws + h->L.off_ay;
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "stream synchronise");
     if (h->prm.precision == LBM_F64) {
@@ -403,6 +466,7 @@ lbm_status lbm_set_force_profile(lbm_handle* h, const double* ay) {
 
 lbm_status lbm_totals(lbm_handle* h, double* sum_f, double* sum_g) {
     if (!h || !sum_f || !sum_g) return h ? fail(h, LBM_ERR_ARG, "null output") : LBM_ERR_ARG;
+    LBM_POPS(h);
     cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         return lbm::launch_totals(k, (const S*)h->buf(h->cur), h->prm.sigma * h->d.T0, h->partial(), h->out(),
@@ -448,12 +512,14 @@ uint64_t params_hash(const lbm_params& p) {
 
 struct CkptHeader {
     char magic[8];          // "LBMCKPT1"
-    uint32_t version;       // 1
+    uint32_t version;       // 2
     int32_t precision;
     int32_t nx, ny, pitch, has_eps;
     int64_t steps;
     uint64_t params_hash;
-    uint64_t payload_bytes; // populations (17 planes) then the porosity field
+    uint64_t payload_bytes; // state planes (17 populations or 9 moments) then the porosity field
+    int32_t state_kind;     // 0 populations, 1 moments
+    int32_t sources;        // moments: 1 once a step has run (0 right after set_fields)
 };
 
 }  // namespace
@@ -463,7 +529,9 @@ extern "C" {
 lbm_status lbm_checkpoint(lbm_handle* h, const char* path, int save) {
     if (!h || !path) return h ? fail(h, LBM_ERR_ARG, "null path") : LBM_ERR_ARG;
     const size_t es = elem_size(h->prm.precision);
-    const size_t pop_bytes = h->L.plane_elems * es * lbm::NPLANES;
+    const bool mk = h->moments_kind();
+    const size_t pop_bytes = h->L.plane_elems * es * (mk ? lbm::kMPlanes : lbm::NPLANES);
+    void* state = mk ? h->mom(h->mcur) : h->buf(h->cur);
     const size_t eps_es = h->prm.precision == LBM_F64 ? 8 : 4;
     const void* eps_dev = h->prm.precision == LBM_F64 ? (const void*)h->k64.eps_field : (const void*)h->k32.eps_field;
     if (save) {
@@ -471,13 +539,15 @@ lbm_status lbm_checkpoint(lbm_handle* h, const char* path, int save) {
         if (s != LBM_OK) return s;
         const size_t eps_bytes = eps_dev ? h->N() * eps_es : 0;
         std::string payload(pop_bytes + eps_bytes, '\0');
-        LBM_CUDA(h, cudaMemcpy(&payload[0], h->buf(h->cur), pop_bytes, cudaMemcpyDeviceToHost), "state read");
+        LBM_CUDA(h, cudaMemcpy(&payload[0], state, pop_bytes, cudaMemcpyDeviceToHost), "state read");
         if (eps_dev)
             LBM_CUDA(h, cudaMemcpy(&payload[pop_bytes], eps_dev, eps_bytes, cudaMemcpyDeviceToHost), "field read");
         CkptHeader hd;
         memset(&hd, 0, sizeof(hd));
         memcpy(hd.magic, "LBMCKPT1", 8);
-        hd.version = 1;
+        hd.version = 2;
+        hd.state_kind = mk ? 1 : 0;
+        hd.sources = mk ? (h->msources ? 1 : 0) : 1;
         hd.precision = h->prm.precision;
         hd.nx = h->prm.nx;
         hd.ny = h->prm.ny;
@@ -498,12 +568,12 @@ lbm_status lbm_checkpoint(lbm_handle* h, const char* path, int save) {
     FILE* f = fopen(path, "rb");
     if (!f) return fail(h, LBM_ERR_ARG, std::string("cannot open ") + path);
     CkptHeader hd;
-    if (fread(&hd, sizeof(hd), 1, f) != 1 || memcmp(hd.magic, "LBMCKPT1", 8) != 0 || hd.version != 1) {
+    if (fread(&hd, sizeof(hd), 1, f) != 1 || memcmp(hd.magic, "LBMCKPT1", 8) != 0 || hd.version != 2) {
         fclose(f);
         return fail(h, LBM_ERR_ARG, "not a checkpoint of this library");
     }
     if (hd.precision != h->prm.precision || hd.nx != h->prm.nx || hd.ny != h->prm.ny || hd.pitch != h->L.pitch ||
-        hd.params_hash != params_hash(h->prm)) {
+        hd.params_hash != params_hash(h->prm) || hd.state_kind != (mk ? 1 : 0)) {
         fclose(f);
         return fail(h, LBM_ERR_ARG, "checkpoint belongs to a different problem or precision");
     }
@@ -520,7 +590,11 @@ lbm_status lbm_checkpoint(lbm_handle* h, const char* path, int save) {
     if (crc32_update(0, (const unsigned char*)payload.data(), payload.size()) != crc)
         return fail(h, LBM_ERR_ARG, "checkpoint corrupted (CRC-32 mismatch)");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "stream synchronise");
-    LBM_CUDA(h, cudaMemcpy(h->buf(h->cur), payload.data(), pop_bytes, cudaMemcpyHostToDevice), "state write");
+    LBM_CUDA(h, cudaMemcpy(state, payload.data(), pop_bytes, cudaMemcpyHostToDevice), "state write");
+    if (mk) {
+        h->msources = hd.sources != 0;
+        h->pops_valid = false;
+    }
     if (hd.has_eps) {
         char* area = h->ws + h->L.off_eps;
         LBM_CUDA(h, cudaMemcpy(area, payload.data() + pop_bytes, h->N() * eps_es, cudaMemcpyHostToDevice), "field write");
@@ -596,6 +670,7 @@ extern "C" lbm_status lbm_nusselt_noalloc(lbm_handle* h, int side, double* nu_me
     const int n = side <= 1 ? h->prm.ny : h->prm.nx;
     const int across = side <= 1 ? h->prm.nx : h->prm.ny;
     if (across < 3) return fail(h, LBM_ERR_ARG, "the one-sided difference needs 3 nodes");
+    LBM_POPS(h);
     if (n > kNoAllocMaxNodes)
         return fail(h, LBM_ERR_ARG,
                     "wall longer than the 65536 nodes the static scratch of lbm_nusselt_noalloc holds");

@@ -134,6 +134,8 @@ std::vector<int> make_bounds(const std::vector<double>& cum, int grid) {
 lbm_status batch_layout(const lbm_params* p, int n, lbm_batch* b, std::string* why) {
     const int prec = p[0].precision;
     if (prec != LBM_F64 && prec != LBM_F32) { *why = "batches store FP64 or FP32 populations"; return LBM_ERR_ARG; }
+    for (int c = 0; c < n; ++c)
+        if (p[c].moment_state) { *why = "batches store populations (moment_state must be 0)"; return LBM_ERR_ARG; }
     b->n = n;
     b->precision = prec;
     b->prm.assign(p, p + n);

@@ -210,6 +210,18 @@ __device__ __forceinline__ WallInfo classify(const KConst<R>& k, int x, int y) {
     return w;
 }
 
+template <class R>
+__device__ __forceinline__ bool is_wall(const KConst<R>& k, int x, int y) {
+    return (x == 0 && k.bc[SW] != BC_PERIODIC) || (x == k.nx - 1 && k.bc[SE] != BC_PERIODIC) ||
+           (y == 0 && k.bc[SS] != BC_PERIODIC) || (y == k.ny - 1 && k.bc[SN] != BC_PERIODIC);
+}
+
+// Column x is a W or E wall column.
+template <class R>
+__device__ __forceinline__ bool is_wall_x(const KConst<R>& k, int x) {
+    return (x == 0 && k.bc[SW] != BC_PERIODIC) || (x == k.nx - 1 && k.bc[SE] != BC_PERIODIC);
+}
+
 // Post-streaming populations of node (x, y): f_i and g_i pulled from x - c_i.
 template <class R, class S>
 __device__ __forceinline__ void pull(const KConst<R>& k, const S* __restrict__ src, int x, int y,
@@ -604,13 +616,114 @@ __device__ __forceinline__ void apply_eps(KConst<R>& k, R eps) {
     k.h0_uu = itT * (R(4) / R(9)) * R(1.5) * c.inv_eps;
 }
 
+// Macroscopic state of a node in the fast path: the moments the step
+// computes after streaming (Sec. 3.1-3.3) plus the derived quantities the
+// collision uses.
+template <class R>
+struct FastState {
+    R th, T, ux, uy, uu, Fx, Fy, uF, p, ep, Sxx, Syy, Sxy, gx, gy;
+};
+
+// Planes of the moment state (tau = 1 storage): p, u, S, T - T0, grad T.
+enum MomentPlane { MP = 0, MUX, MUY, MSXX, MSYY, MSXY, MTH, MGX, MGY };
+constexpr int kMPlanes = 9;
+
+// Moments of an interior node from its pulled populations (f[1..8], h[0..8]),
+// in the fast path's arrangement of node_moments.
+template <class R>
+__device__ __forceinline__ FastState<R> fast_moments(const KConst<R>& k, const R* f, const R* h, int y) {
+    FastState<R> s;
+    const R sh = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+    s.th = (sh + R(0.5) * k.Q) * k.inv_sigma;
+    s.T = k.T0 + s.th;
+    const R a13 = f[1] + f[3], a24 = f[2] + f[4], d58 = (f[5] + f[7]) + (f[6] + f[8]);
+    const R sf = a13 + a24 + d58;
+    const R mx = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
+    const R my = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+    const R Pxx = a13 + d58, Pyy = a24 + d58;
+    const R Pxy = (f[5] + f[7]) - (f[6] + f[8]);
+    const R Gy = k.gbeta * s.th + row_ay(k, y);
+    const R vx = mx * k.inv_rho0 + k.half_eps_ax;
+    const R vy = my * k.inv_rho0 + k.half_eps * Gy;
+    const R vmag = sqrt(vx * vx + vy * vy);
+    const R iden = R(1) / (k.c0 + sqrt(k.c0sq + k.c1 * vmag));
+    s.ux = vx * iden;
+    s.uy = vy * iden;
+    if (!isfinite(s.th + s.ux + s.uy)) atomicOr(k.flag, 1);
+    s.uu = s.ux * s.ux + s.uy * s.uy;
+    const R drag = k.e_nuK + k.e_FK * sqrt(s.uu);
+    s.Fx = k.eps * k.ax - drag * s.ux;
+    s.Fy = k.eps * Gy - drag * s.uy;
+    s.uF = s.ux * s.Fx + s.uy * s.Fy;
+    const R p = k.p_pref * sf - k.p_uF * s.uF - k.p_uu * s.uu;
+    s.p = p;
+    s.ep = k.eps * p;
+    const R re = k.rho0 * k.inv_eps;
+    s.Sxx = (Pxx - s.ep + re * s.ux * (s.Fx - s.ux)) * k.invD;
+    s.Syy = (Pyy - s.ep + re * s.uy * (s.Fy - s.uy)) * k.invD;
+    s.Sxy = (Pxy + re * (R(0.5) * (s.ux * s.Fy + s.Fx * s.uy) - s.ux * s.uy)) * k.invD;
+    const R hx = (h[1] - h[3]) + (h[5] - h[7]) + (h[8] - h[6]);
+    const R hy = (h[2] - h[4]) + (h[5] - h[7]) + (h[6] - h[8]);
+    const R qs = R(0.5) * k.Q * k.inv_sigma;
+    const R Nx = hx + s.T * (R(0.5) * s.Fx - s.ux) + qs * s.ux;
+    const R Ny = hy + s.T * (R(0.5) * s.Fy - s.uy) + qs * s.uy;
+    const R a = k.a_const - R(0.5) * s.ep * k.inv_rho0;
+    const R ia = R(1) / a;
+    const R t = k.bcoef * (s.ux * Nx + s.uy * Ny) / (a - k.bcoef * s.uu);
+    s.gx = (Nx + t * s.ux) * ia;
+    s.gy = (Ny + t * s.uy) * ia;
+    return s;
+}
+
+// Collision of one node from its state: h_i* = (1 - 1/tau) h_i +
+// [h_i^eq/tau + source_i], the bracket split into the parts even and odd
+// under c_i -> -c_i so that each pair of opposite directions shares one
+// evaluation.  TAU1: tau_f = tau_T = 1, where the first term vanishes and
+// f, h are not read.  SOURCES = false drops the force and heat-source terms
+// (F_i, P_i, Q_i) and keeps the equilibria alone.
+template <class R, bool TAU1, bool SOURCES = true>
+__device__ __forceinline__ void fast_collide(const KConst<R>& k, const FastState<R>& s, const R* f,
+                                             const R* h, R* fo, R* ho) {
+    const R uF = SOURCES ? s.uF : R(0);
+    const R Fx = SOURCES ? s.Fx : R(0), Fy = SOURCES ? s.Fy : R(0);
+    const R kQ = SOURCES ? k.h_kQ : R(0), uQ = SOURCES ? k.h_uQ : R(0), k0Q = SOURCES ? k.h0_kQ : R(0);
+    const R T = s.T, ep = s.ep, uu = s.uu, ux = s.ux, uy = s.uy, gx = s.gx, gy = s.gy;
+    const R EF0 = k.fA_ep * ep - k.fA_uu * uu - k.fA_tr * (s.Sxx + s.Syy) - k.fA_uF * uF;
+    const R EH0 = k.h_sig * s.th - k.h_uu * T * uu + k.h_pT * T * ep + kQ;
+    const R Kc = k.h_cu2 * T;
+    const R Ku = k.h_u3 * T + (SOURCES ? k.h_ug * (ux * gx + uy * gy) : R(0)) + uQ;
+    const R epr = ep * k.inv_rho0;
+    const R Wx = SOURCES ? T * Fx + epr * gx : R(0), Wy = SOURCES ? T * Fy + epr * gy : R(0);
+    auto pair = [&](int i, int j, R w, R cu, R cF, R ScS, R cg, R cW) {
+        const R evF = EF0 + k.f_cu2 * cu * cu + k.f_ScS * ScS + k.f_cucF * cu * cF;
+        const R odF = k.f_cu * cu + k.f_cF * cF;
+        const R evH = EH0 + Kc * cu * cu;
+        const R odH = Ku * cu + k.h_g * cg + k.h_W * cW;
+        if (TAU1) {
+            fo[i] = w * (evF + odF);
+            fo[j] = w * (evF - odF);
+            ho[i] = w * (evH + odH);
+            ho[j] = w * (evH - odH);
+        } else {
+            fo[i] = k.omf * f[i] + w * (evF + odF);
+            fo[j] = k.omf * f[j] + w * (evF - odF);
+            ho[i] = k.omT * h[i] + w * (evH + odH);
+            ho[j] = k.omT * h[j] + w * (evH - odH);
+        }
+    };
+    const R w1 = R(1) / R(9), w5 = R(1) / R(36);
+    pair(1, 3, w1, ux, Fx, s.Sxx, gx, Wx);
+    pair(2, 4, w1, uy, Fy, s.Syy, gy, Wy);
+    pair(5, 7, w5, ux + uy, Fx + Fy, s.Sxx + s.Syy + R(2) * s.Sxy, gx + gy, Wx + Wy);
+    pair(6, 8, w5, uy - ux, Fy - Fx, s.Sxx + s.Syy - R(2) * s.Sxy, gy - gx, Wy - Wx);
+    const R c0 = k.h0_sig * s.th - k.h0_uu * T * uu - k.h0_pT * T * ep + k0Q;
+    ho[0] = TAU1 ? c0 : k.omT * h[0] + c0;
+}
+
 // Interior node of one step, fast path.  Same arithmetic as node_moments +
-// eq_terms + BGK collision, rearranged for the GPU:
-//  * the nine pull sources are 32-bit offsets from the node (periodic wrap by
-//    per-thread deltas), plane strides are uniform across the launch;
-//  * the collision is written as h_i* = (1 - 1/tau) h_i + [h_i^eq/tau + source_i]
-//    and the bracket is split into the parts that are even and odd under
-//    c_i -> -c_i, so each pair of opposite directions shares one evaluation.
+// eq_terms + BGK collision, rearranged for the GPU: the nine pull sources are
+// 32-bit offsets from the node (periodic wrap by per-thread deltas), plane
+// strides are uniform across the launch; then fast_moments and fast_collide.
 template <class R, class S>
 __device__ __forceinline__ void interior_update(const KConst<R>& k, const S* __restrict__ src,
                                                 S* __restrict__ dst, int x, int y, uint32_t step) {
@@ -628,71 +741,9 @@ __device__ __forceinline__ void interior_update(const KConst<R>& k, const S* __r
     for (int i = 1; i < 9; ++i) f[i] = load_pop<S, R>(c + ((i - 1) * pl + o[i]), sc);
 #pragma unroll
     for (int i = 0; i < 9; ++i) h[i] = load_pop<S, R>(c + ((8 + i) * pl + o[i]), sc);
-
-    // moments (Sec. 3.1-3.3)
-    const R sh = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
-    const R th = (sh + R(0.5) * k.Q) * k.inv_sigma;
-    const R T = k.T0 + th;
-    const R a13 = f[1] + f[3], a24 = f[2] + f[4], d58 = (f[5] + f[7]) + (f[6] + f[8]);
-    const R sf = a13 + a24 + d58;
-    const R mx = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
-    const R my = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
-    const R Pxx = a13 + d58, Pyy = a24 + d58;
-    const R Pxy = (f[5] + f[7]) - (f[6] + f[8]);
-    const R Gy = k.gbeta * th + row_ay(k, y);
-    const R vx = mx * k.inv_rho0 + k.half_eps_ax;
-    const R vy = my * k.inv_rho0 + k.half_eps * Gy;
-    const R vmag = sqrt(vx * vx + vy * vy);
-    const R iden = R(1) / (k.c0 + sqrt(k.c0sq + k.c1 * vmag));
-    const R ux = vx * iden, uy = vy * iden;
-    if (!isfinite(th + ux + uy)) atomicOr(k.flag, 1);
-    const R uu = ux * ux + uy * uy;
-    const R drag = k.e_nuK + k.e_FK * sqrt(uu);
-    const R Fx = k.eps * k.ax - drag * ux;
-    const R Fy = k.eps * Gy - drag * uy;
-    const R uF = ux * Fx + uy * Fy;
-    const R p = k.p_pref * sf - k.p_uF * uF - k.p_uu * uu;
-    const R ep = k.eps * p;
-    const R re = k.rho0 * k.inv_eps;
-    const R Sxx = (Pxx - ep + re * ux * (Fx - ux)) * k.invD;
-    const R Syy = (Pyy - ep + re * uy * (Fy - uy)) * k.invD;
-    const R Sxy = (Pxy + re * (R(0.5) * (ux * Fy + Fx * uy) - ux * uy)) * k.invD;
-    const R hx = (h[1] - h[3]) + (h[5] - h[7]) + (h[8] - h[6]);
-    const R hy = (h[2] - h[4]) + (h[5] - h[7]) + (h[6] - h[8]);
-    const R qs = R(0.5) * k.Q * k.inv_sigma;
-    const R Nx = hx + T * (R(0.5) * Fx - ux) + qs * ux;
-    const R Ny = hy + T * (R(0.5) * Fy - uy) + qs * uy;
-    const R a = k.a_const - R(0.5) * ep * k.inv_rho0;
-    const R ia = R(1) / a;
-    const R t = k.bcoef * (ux * Nx + uy * Ny) / (a - k.bcoef * uu);
-    const R gx = (Nx + t * ux) * ia;
-    const R gy = (Ny + t * uy) * ia;
-
-    // collision, pairs of opposite directions
-    const R EF0 = k.fA_ep * ep - k.fA_uu * uu - k.fA_tr * (Sxx + Syy) - k.fA_uF * uF;
-    const R EH0 = k.h_sig * th - k.h_uu * T * uu + k.h_pT * T * ep + k.h_kQ;
-    const R Kc = k.h_cu2 * T;
-    const R Ku = k.h_u3 * T + k.h_ug * (ux * gx + uy * gy) + k.h_uQ;
-    const R epr = ep * k.inv_rho0;
-    const R Wx = T * Fx + epr * gx, Wy = T * Fy + epr * gy;
+    const FastState<R> s = fast_moments(k, f, h, y);
     R fo[9], ho[9];
-    auto pair = [&](int i, int j, R w, R cu, R cF, R ScS, R cg, R cW) {
-        const R evF = EF0 + k.f_cu2 * cu * cu + k.f_ScS * ScS + k.f_cucF * cu * cF;
-        const R odF = k.f_cu * cu + k.f_cF * cF;
-        fo[i] = k.omf * f[i] + w * (evF + odF);
-        fo[j] = k.omf * f[j] + w * (evF - odF);
-        const R evH = EH0 + Kc * cu * cu;
-        const R odH = Ku * cu + k.h_g * cg + k.h_W * cW;
-        ho[i] = k.omT * h[i] + w * (evH + odH);
-        ho[j] = k.omT * h[j] + w * (evH - odH);
-    };
-    const R w1 = R(1) / R(9), w5 = R(1) / R(36);
-    pair(1, 3, w1, ux, Fx, Sxx, gx, Wx);
-    pair(2, 4, w1, uy, Fy, Syy, gy, Wy);
-    pair(5, 7, w5, ux + uy, Fx + Fy, Sxx + Syy + R(2) * Sxy, gx + gy, Wx + Wy);
-    pair(6, 8, w5, uy - ux, Fy - Fx, Sxx + Syy - R(2) * Sxy, gy - gx, Wy - Wx);
-    ho[0] = k.omT * h[0] + (k.h0_sig * th - k.h0_uu * T * uu - k.h0_pT * T * ep + k.h0_kQ);
-
+    fast_collide<R, false>(k, s, f, h, fo, ho);
     Dither dither((uint32_t)at, step);
     store_planes<S, R>(dst + at, pl, fo, ho, k.inv_scale, &dither);
 }

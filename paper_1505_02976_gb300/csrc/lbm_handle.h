@@ -18,6 +18,11 @@ struct lbm_handle {
     bool owns_ws;
     int cur;
     int64_t steps, launches;
+    // moment state: current buffer, whether it holds force/source terms (not
+    // after set_fields), and whether the expansion in buf(0) is up to date
+    int mcur;
+    bool msources, pops_valid;
+    int msegments;  // row segments per band of the moment step
     bool nonfinite;
     lbm::KConst<double> k64;
     lbm::KConst<float> k32;
@@ -25,6 +30,8 @@ struct lbm_handle {
     std::string err;
 
     void* buf(int i) const { return ws + L.off_buf[i]; }
+    void* mom(int i) const { return ws + L.off_mom[i]; }
+    bool moments_kind() const { return prm.moment_state != 0; }
     double* fields() const { return (double*)(ws + L.off_fields); }
     double* snap() const { return (double*)(ws + L.off_snap); }
     double* nu() const { return (double*)(ws + L.off_nu); }

@@ -78,8 +78,12 @@ inline lbm_status check_shape(const lbm_params* p, std::string* why) {
         *why = "lattice too large for 32-bit plane offsets (17 nx ny < 2^31)";
         return LBM_ERR_ARG;
     }
-    if (p->precision < LBM_F64 || p->precision > LBM_F16 || p->reserved != 0) {
-        *why = "unknown precision";
+    if (p->precision < LBM_F64 || p->precision > LBM_F16 || p->moment_state < 0 || p->moment_state > 1) {
+        *why = "unknown precision or state kind";
+        return LBM_ERR_ARG;
+    }
+    if (p->moment_state && !(p->tau_f == 1.0 && p->tau_T == 1.0 && p->precision != LBM_F16)) {
+        *why = "moment storage needs tau_f = tau_T = 1 and FP32 or FP64";
         return LBM_ERR_ARG;
     }
     return LBM_OK;
@@ -95,6 +99,7 @@ struct Layout {
     int pitch;
     size_t plane_elems, buf_bytes;
     size_t off_buf[2], off_fields, off_snap, off_nu, off_partial, off_eps, off_ay, off_out, off_flag, total;
+    size_t off_mom[2], mom_bytes;  // moment state: two 9-plane buffers; off_buf[0] = off_buf[1] = expansion
 };
 
 inline Layout layout(const lbm_params* p) {
@@ -107,7 +112,16 @@ inline Layout layout(const lbm_params* p) {
     const size_t N = (size_t)p->nx * p->ny;
     size_t o = 0;
     L.off_buf[0] = o; o += L.buf_bytes;
-    L.off_buf[1] = o; o += L.buf_bytes;
+    if (p->moment_state) {
+        L.off_buf[1] = L.off_buf[0];
+        L.mom_bytes = align256(L.plane_elems * es * lbm::kMPlanes);
+        L.off_mom[0] = o; o += L.mom_bytes;
+        L.off_mom[1] = o; o += L.mom_bytes;
+    } else {
+        L.off_buf[1] = o; o += L.buf_bytes;
+        L.mom_bytes = 0;
+        L.off_mom[0] = L.off_mom[1] = 0;
+    }
     L.off_fields = o; o += align256(4 * N * sizeof(double));
     L.off_snap = o; o += align256(3 * N * sizeof(double));
     L.off_nu = o; o += align256((size_t)(p->nx > p->ny ? p->nx : p->ny) * sizeof(double));

@@ -96,6 +96,27 @@ template <class R, class S>
 cudaError_t launch_nusselt_batch(const BatchCavity<R>* cav, int n, const S* src, int side,
                                  double* out, cudaStream_t st);
 
+// --------------------------------------------------- moment state (tau = 1)
+// One step of the moment state (9 planes: p, u, S, T - T0, grad T) from src
+// to dst; sources = false when src is the state written by launch_init_m
+// (equilibria without force and source terms).  segments: row segments per
+// band (clamped so that each keeps >= 3 rows).
+template <class R>
+cudaError_t launch_step_m(const KConst<R>& k, const R* src, R* dst, bool sources, int segments, cudaStream_t st);
+
+// Post-collision populations (17 planes, as the population kernels store
+// them) of the moment state src.
+template <class R>
+cudaError_t launch_expand_m(const KConst<R>& k, const R* src, R* dst, bool sources, cudaStream_t st);
+
+template <class R>
+cudaError_t launch_init_m(const KConst<R>& k, R* dst, const double* T, const double* ux, const double* uy,
+                          double T_init, cudaStream_t st);
+
+// Row segments per band that fill the GPU's resident blocks once.
+template <class R>
+int moment_segments_default(const KConst<R>& k);
+
 // Resident blocks per SM of the batched step kernel.
 template <class R, class S>
 int batch_blocks_per_sm(int tile_x);

@@ -77,11 +77,6 @@ __device__ __noinline__ void wall_update(const KConst<R>& k, const S* __restrict
     store_node(k, dst, (long long)y * k.pitch + x, fo, ho, &dither);
 }
 
-template <class R>
-__device__ __forceinline__ bool is_wall(const KConst<R>& k, int x, int y) {
-    return (x == 0 && k.bc[SW] != BC_PERIODIC) || (x == k.nx - 1 && k.bc[SE] != BC_PERIODIC) ||
-           (y == 0 && k.bc[SS] != BC_PERIODIC) || (y == k.ny - 1 && k.bc[SN] != BC_PERIODIC);
-}
 
 // The fused step: one thread per node; interior nodes take the fast path,
 // wall nodes the NEES path.

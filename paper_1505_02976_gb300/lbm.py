@@ -45,7 +45,7 @@ class lbm_params(C.Structure):
     _fields_ = [
         ("nx", C.c_int32), ("ny", C.c_int32), ("bc", C.c_int32 * 4),
         ("forchheimer", C.c_int32), ("da_infinite", C.c_int32),
-        ("precision", C.c_int32), ("reserved", C.c_int32),
+        ("precision", C.c_int32), ("moment_state", C.c_int32),
         ("Ra", C.c_double), ("Pr", C.c_double), ("Da", C.c_double), ("J", C.c_double),
         ("eps", C.c_double), ("sigma", C.c_double), ("Ma", C.c_double),
         ("tau_f", C.c_double), ("tau_T", C.c_double),
@@ -99,7 +99,7 @@ def load(build_if_missing: bool = True):
     L.lbm_totals.argtypes = [H, dp, dp]
     L.lbm_checkpoint.argtypes = [H, C.c_char_p, C.c_int]
     L.lbm_set_force_profile.argtypes = [H, C.c_void_p]
-    L.lbm_stream_function.argtypes = [H, C.c_void_p, C.c_int, dp]
+    L.lbm_stream_function.argtypes = [H, C.c_void_p, C.c_int, C.c_void_p]
     B = C.c_void_p
     L.lbm_batch_workspace_size.argtypes = [P, C.c_int32, C.POINTER(C.c_size_t)]
     L.lbm_batch_create.argtypes = [P, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(B)]
@@ -131,8 +131,12 @@ def _nan(v):
     return float("nan") if v is None else float(v)
 
 
-def params_from_problem(p: dict, precision: str = "f32") -> lbm_params:
-    """Marshal a problem dict (``workloads.problem``) into ``lbm_params``."""
+STATES = ("populations", "moments")
+
+
+def params_from_problem(p: dict, precision: str = "f32", state: str = "populations") -> lbm_params:
+    """Marshal a problem dict (``workloads.problem``) into ``lbm_params``;
+    ``state="moments"`` selects the moment-state storage (tau = 1 only)."""
     s = lbm_params()
     s.nx, s.ny = int(p["nx"]), int(p["ny"])
     for k, b in enumerate(p["bc"]):
@@ -140,7 +144,9 @@ def params_from_problem(p: dict, precision: str = "f32") -> lbm_params:
     s.forchheimer = int(p["forchheimer"])
     s.da_infinite = int(p["da_infinite"])
     s.precision = PRECISION[precision]
-    s.reserved = 0
+    if state not in STATES:
+        raise ValueError(f"state {state!r} not in {STATES}")
+    s.moment_state = int(state == "moments")
     for name in ("Ra", "Pr", "Da", "J", "eps", "sigma", "Ma", "tau_f", "tau_T", "Th", "Tc",
                  "T_init", "rho0", "Q", "ax", "ay", "Ra_I"):
         setattr(s, name, float(p[name]))
@@ -168,9 +174,9 @@ def lbm_derived(p: dict) -> dict:
     return dict(zip(DERIVED_KEYS, list(out)))
 
 
-def lbm_workspace_size(p: dict, precision: str = "f32") -> int:
+def lbm_workspace_size(p: dict, precision: str = "f32", state: str = "populations") -> int:
     n = C.c_size_t()
-    _check(load().lbm_workspace_size(C.byref(params_from_problem(p, precision)), C.byref(n)))
+    _check(load().lbm_workspace_size(C.byref(params_from_problem(p, precision, state)), C.byref(n)))
     return int(n.value)
 
 
@@ -189,7 +195,8 @@ class Lattice:
     ``Lattice(problem, precision)`` creates the handle with a torch-allocated
     workspace on ``device`` and the current torch stream of that device."""
 
-    def __init__(self, problem: dict, precision: str = "f32", device: int = 0, stream=None):
+    def __init__(self, problem: dict, precision: str = "f32", device: int = 0, stream=None,
+                 state: str = "populations"):
         import torch
 
         if not torch.cuda.is_available():
@@ -198,9 +205,10 @@ class Lattice:
         self.problem = dict(problem)
         self.precision = precision
         self.nx, self.ny = int(problem["nx"]), int(problem["ny"])
-        self.params = params_from_problem(problem, precision)
+        self.state = state
+        self.params = params_from_problem(problem, precision, state)
         self.device = torch.device("cuda", device)
-        nbytes = lbm_workspace_size(problem, precision)
+        nbytes = lbm_workspace_size(problem, precision, state)
         with torch.cuda.device(self.device):
             self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -41,7 +41,7 @@ def test_params_struct_layout_matches_header():
     assert lbm.load().lbm_params_default(C.byref(p)) == 0
     assert (p.nx, p.ny) == (32, 32)
     assert list(p.bc) == [1, 1, 2, 2]
-    assert p.precision == 1 and p.reserved == 0
+    assert p.precision == 1 and p.moment_state == 0
     assert (p.Ra, p.Da, p.eps, p.Pr, p.Ma) == (1e3, 1e-2, 0.6, 1.0, 0.1)
     assert math.isnan(p.A) and math.isnan(p.K)
     assert list(p.T_bc) == [1.0, 0.0, 1.0, 0.0]
@@ -100,3 +100,17 @@ def test_no_cpu_fallback_without_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(lbm.LbmError):
         lbm.Lattice(W.cavity(32, 1e3, 1e-2, 0.6))
+
+
+def test_moment_state_parameters_are_checked_on_the_host():
+    p = W.cavity(256, 1e6, 1e-4, 0.4)
+    pop = lbm.lbm_workspace_size(p, "f32")
+    mom = lbm.lbm_workspace_size(p, "f32", "moments")
+    plane = 256 * 256 * 4
+    # one population buffer (17 planes) for the expansion plus two 9-plane moment buffers
+    assert mom - pop == pytest.approx(plane, rel=0.05)
+    for bad, prec in ((dict(p, tau_f=0.9), "f32"), (dict(p, tau_T=1.1), "f64"), (p, "f16")):
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_workspace_size(bad, prec, "moments")
+    with pytest.raises(ValueError):
+        lbm.params_from_problem(p, "f32", "other")

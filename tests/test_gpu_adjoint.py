@@ -20,6 +20,8 @@ import oracle
 from paper_1505_02976_gb300 import lbm
 from paper_1505_02976_gb300 import workloads as W
 
+from oracle_states import sample_nodes, stored_state
+
 pytestmark = pytest.mark.gpu
 
 
@@ -44,17 +46,13 @@ def test_fp32_porosity_field_one_step_sampled():
     n = 256
     p = W.cavity(n, 1e5, 1e-3, 0.6)
     eps = W.gaussian_random_field(n, corr=16.0, seed=1)
+    o, f0, g0 = stored_state(p, W.random_fields(p, seed=3, amp_u=2e-3), "f32", steps=10, eps_field=eps)
     g = lbm.Lattice(p, "f32")
-    g.set_fields(*W.random_fields(p, seed=3, amp_u=2e-3), eps_field=eps)
-    g.step(10)
-    f0, g0 = g.get_state()
+    g.set_fields(eps_field=eps)
+    g.set_state(f0, g0)
     g.step(1)
     f1, g1 = g.get_state()
-    f0[0] = 0.0
-    o = oracle.Oracle.from_state(p, f0, g0, eps_field=eps)
-    rng = np.random.Generator(np.random.PCG64(2))
-    xs = np.r_[rng.integers(0, n, 300), 0, n - 1, 1].astype(np.int32)
-    ys = np.r_[rng.integers(0, n, 300), 0, n - 1, 0].astype(np.int32)
+    xs, ys = sample_nodes(n, n, 300, seed=2)
     fo, go = o.update_nodes(xs, ys)
     assert np.abs(f1[1:, ys, xs].T - fo[:, 1:]).max() <= 1e-6 * np.abs(fo[:, 1:]).max()
     assert np.abs(g1[:, ys, xs].T - go).max() <= 1e-6 * np.abs(go).max()

@@ -15,6 +15,8 @@ import oracle
 from paper_1505_02976_gb300 import lbm
 from paper_1505_02976_gb300 import workloads as W
 
+from oracle_states import sample_nodes, stored_state
+
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
@@ -100,21 +102,16 @@ def test_fp64_boundary_combinations(bc):
 
 
 def test_fp64_one_step_sampled_at_scale():
-    """One step of a 640 x 384 lattice from a random state: every sampled
-    node (walls, corners and interior) against the oracle's node update."""
+    """One step of a 640 x 384 lattice from the oracle's state three steps
+    after a random start: every sampled node (walls, corners and interior)
+    against the oracle's node update."""
     p = W.cavity(640, 1e6, 1e-4, 0.4, ny=384)
-    fields = W.random_fields(p, seed=5, amp_u=5e-3)
+    o, f0, g0 = stored_state(p, W.random_fields(p, seed=5, amp_u=5e-3), "f64", steps=3)
     g = lbm.Lattice(p, "f64")
-    g.set_fields(*fields)
-    g.step(3)
-    f0, g0 = g.get_state()
+    g.set_state(f0, g0)
     g.step(1)
     f1, g1 = g.get_state()
-    f0[0] = 0.0
-    o = oracle.Oracle.from_state(p, f0, g0)
-    rng = np.random.Generator(np.random.PCG64(9))
-    xs = np.r_[rng.integers(0, p["nx"], 300), 0, 0, p["nx"] - 1, p["nx"] - 1, 1, 2, 5].astype(np.int32)
-    ys = np.r_[rng.integers(0, p["ny"], 300), 0, p["ny"] - 1, 0, p["ny"] - 1, 0, p["ny"] - 1, 1].astype(np.int32)
+    xs, ys = sample_nodes(p["nx"], p["ny"], 300, seed=9)
     fo, go = o.update_nodes(xs, ys)
     fg = f1[:, ys, xs].T
     gg = g1[:, ys, xs].T
@@ -139,22 +136,16 @@ def test_fp32_cavity_against_oracle():
 
 def test_fp32_one_step_sampled_at_full_size():
     """The 2048 x 2048 FP32 workload in its benchmark launch configuration:
-    one step from a developed state, sampled nodes against the oracle's node
-    update evaluated in FP64 on the same (FP32-stored) input state."""
+    one step from the oracle's state one step after a random start, rounded
+    to FP32 storage; sampled nodes against the oracle's node update evaluated
+    in FP64 on the same stored input."""
     p = W.cavity(2048, 1e6, 1e-4, 0.4)
+    o, f0, g0 = stored_state(p, W.random_fields(p, seed=21, amp_u=2e-3, amp_T=0.3), "f32", steps=1)
     g = lbm.Lattice(p, "f32")
-    fields = W.random_fields(p, seed=21, amp_u=2e-3, amp_T=0.3)
-    g.set_fields(*fields)
-    g.step(20)
-    f0, g0 = g.get_state()
+    g.set_state(f0, g0)
     g.step(1)
     f1, g1 = g.get_state()
-    f0[0] = 0.0
-    o = oracle.Oracle.from_state(p, f0, g0)
-    rng = np.random.Generator(np.random.PCG64(10))
-    n = p["nx"]
-    xs = np.r_[rng.integers(0, n, 400), 0, 0, n - 1, n - 1, 1, 2, n - 2].astype(np.int32)
-    ys = np.r_[rng.integers(0, n, 400), 0, n - 1, 0, n - 1, 0, n - 1, 1].astype(np.int32)
+    xs, ys = sample_nodes(p["nx"], p["ny"], 400, seed=10)
     fo, go = o.update_nodes(xs, ys)
     fg = f1[:, ys, xs].T
     gg = g1[:, ys, xs].T
@@ -229,23 +220,20 @@ def test_fp16_cavity_against_oracle():
 
 
 def test_fp16_one_step_sampled_at_full_size():
-    """The 8192 x 8192 FP16 workload: one step from a developed state, sampled
-    nodes against the oracle's node update on the same FP16-stored state.
-    The GPU output is rounded to FP16 stochastically, so each value may differ
-    by one FP16 step of its magnitude (2^-10 relative) plus FP32 rounding."""
+    """The 8192 x 8192 FP16 workload: one step from a random state rounded to
+    FP16 storage, sampled nodes against the oracle's node update on the same
+    stored values.  The GPU output is rounded to FP16 stochastically, so each
+    value may differ by one FP16 step of its magnitude (2^-10 relative) plus
+    FP32 rounding."""
     n = 8192
     p = W.config_problem(W.CONFIG_FP16_CAVITY)
+    o, f0, g0 = stored_state(p, W.random_fields(p, seed=31, amp_u=2e-3, amp_T=0.3), "f16")
     g = lbm.Lattice(p, "f16")
-    g.set_fields(*W.random_fields(p, seed=31, amp_u=2e-3, amp_T=0.3))
-    g.step(5)
-    f0, g0 = g.get_state()
+    g.set_state(f0, g0)
+    del f0, g0
     g.step(1)
     f1, g1 = g.get_state()
-    f0[0] = 0.0
-    o = oracle.Oracle.from_state(p, f0, g0, copy=False)
-    rng = np.random.Generator(np.random.PCG64(12))
-    xs = np.r_[rng.integers(0, n, 400), 0, 0, n - 1, n - 1, 1, 2, n - 2].astype(np.int32)
-    ys = np.r_[rng.integers(0, n, 400), 0, n - 1, 0, n - 1, 0, n - 1, 1].astype(np.int32)
+    xs, ys = sample_nodes(n, n, 400, seed=12)
     fo, go = o.update_nodes(xs, ys)
     fg = f1[:, ys, xs].T
     gg = g1[:, ys, xs].T
