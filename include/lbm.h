@@ -117,6 +117,12 @@ typedef struct {
  * other call behaves as with populations (lbm_get_state returns the
  * post-collision populations the moments define). */
 
+/* Row segments per column band of the moment-state step (segments >= 1;
+ * 0 restores the default, which fills the GPU's resident blocks once).
+ * Every choice computes the same values.  LBM_ERR_ARG on a population
+ * handle. */
+lbm_status lbm_set_moment_segments(lbm_handle* h, int32_t segments);
+
 /* Fill p with the paper's defaults (Sec. 4): the 32 x 32 porous cavity,
  * hot W wall T = 1, cold E wall T = 0, adiabatic S and N, no slip, rho0 = 1,
  * J = sigma = 1, tau_f = tau_T = 1, Ma = 0.1, Ra = 1e3, Da = 1e-2,

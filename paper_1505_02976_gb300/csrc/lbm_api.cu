@@ -300,6 +300,16 @@ lbm_status lbm_step(lbm_handle* h, int64_t n) {
     return LBM_OK;
 }
 
+lbm_status lbm_set_moment_segments(lbm_handle* h, int32_t segments) {
+    if (!h) return LBM_ERR_ARG;
+    if (!h->moments_kind() || segments < 0) return fail(h, LBM_ERR_ARG, "not a moment-state handle, or segments < 0");
+    if (segments == 0)
+        segments = h->prm.precision == LBM_F64 ? lbm::moment_segments_default(h->k64)
+                                               : lbm::moment_segments_default(h->k32);
+    h->msegments = segments;
+    return LBM_OK;
+}
+
 lbm_status lbm_sync(lbm_handle* h) {
     if (!h) return LBM_ERR_ARG;
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "stream synchronise");

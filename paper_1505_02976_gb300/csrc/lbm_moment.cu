@@ -27,6 +27,11 @@ namespace lbm {
 
 constexpr int kMBlock = 128;           // threads = expansion columns of a band
 constexpr int kMBand = kMBlock - 2;    // output columns of a band, at most
+// Expanded rows kept in shared memory: rows y - 1, y, y + 1 while row y is
+// updated, and a barrier after the update frees the slot of row y - 1.  (A
+// fourth slot would save that barrier but costs two resident blocks per SM,
+// which measured slower.)
+constexpr int kMRing = 3;
 template <class R> struct MomentOccupancy { static constexpr int blocks = 8; };
 template <> struct MomentOccupancy<double> { static constexpr int blocks = 2; };
 
@@ -55,17 +60,20 @@ __device__ __forceinline__ FastState<R> state_from_moments(const KConst<R>& k, c
     return s;
 }
 
+// Plane strides are 32-bit (9 planes of ny * pitch < 2^31 elements).
 template <class R>
 __device__ __forceinline__ void store_moments(const KConst<R>& k, R* dst, long long at, const FastState<R>& s) {
-    dst[MP * k.plane + at] = s.p;
-    dst[MUX * k.plane + at] = s.ux;
-    dst[MUY * k.plane + at] = s.uy;
-    dst[MSXX * k.plane + at] = s.Sxx;
-    dst[MSYY * k.plane + at] = s.Syy;
-    dst[MSXY * k.plane + at] = s.Sxy;
-    dst[MTH * k.plane + at] = s.th;
-    dst[MGX * k.plane + at] = s.gx;
-    dst[MGY * k.plane + at] = s.gy;
+    R* d = dst + at;
+    const int pl = k.plane32;
+    d[MP * pl] = s.p;
+    d[MUX * pl] = s.ux;
+    d[MUY * pl] = s.uy;
+    d[MSXX * pl] = s.Sxx;
+    d[MSYY * pl] = s.Syy;
+    d[MSXY * pl] = s.Sxy;
+    d[MTH * pl] = s.th;
+    d[MGX * pl] = s.gx;
+    d[MGY * pl] = s.gy;
 }
 
 // Boundary state of wall node (x, y) from the new moments of x_f and the new
@@ -119,7 +127,7 @@ k_step_m(const __grid_constant__ KConst<R> k, const R* __restrict__ src, R* dst)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* ring = reinterpret_cast<R*>(smem_raw);  // [3][17][kMBlock]
+    R* ring = reinterpret_cast<R*>(smem_raw);  // [kMRing][17][kMBlock]
     const int tid = threadIdx.x;
     const Tile t = tile_of(k.nx, k.ny);
     const bool perx = k.bc[SW] == BC_PERIODIC, pery = k.bc[SS] == BC_PERIODIC;
@@ -135,16 +143,24 @@ k_step_m(const __grid_constant__ KConst<R> k, const R* __restrict__ src, R* dst)
     const int x = t.x0 - 1 + tid;
     const bool out_col = tid >= 1 && x < t.x1;
 
-    auto expand = [&](int r, int slot) {
-        if (r < 0 || r >= k.ny) {
-            if (!pery) return;
-            r = r < 0 ? r + k.ny : r - k.ny;
-        }
-        if (!xe_ok) return;
-        const long long at = (long long)r * k.pitch + xe;
-        R m[kMPlanes];
+    // row r of the lattice as stored (periodic wrap), or -1 if it does not exist
+    auto row_of = [&](int r) {
+        if (r >= 0 && r < k.ny) return r;
+        if (!pery) return -1;
+        return r < 0 ? r + k.ny : r - k.ny;
+    };
+    // the moments of this thread's expansion node in row r (issued early so
+    // that the loads are in flight while the previous row is processed)
+    auto load_row = [&](int r, R* m) {
+        r = row_of(r);
+        if (r < 0 || !xe_ok) return;
+        const R* s = src + ((long long)r * k.pitch + xe);
 #pragma unroll
-        for (int q = 0; q < kMPlanes; ++q) m[q] = src[q * k.plane + at];
+        for (int q = 0; q < kMPlanes; ++q) m[q] = s[q * k.plane32];
+    };
+    auto expand = [&](int r, int slot, const R* m) {
+        r = row_of(r);
+        if (r < 0 || !xe_ok) return;
         R fo[9], ho[9];
         if constexpr (EPS_FIELD) {
             KConst<R> kc = k;
@@ -199,10 +215,18 @@ k_step_m(const __grid_constant__ KConst<R> k, const R* __restrict__ src, R* dst)
     const bool wallN = !pery && t.y1 == k.ny;          // ... the N wall row
     const bool wallWE = !perx && (t.x0 == 0 || t.x1 == k.nx);
     int sm = 0, s0 = 1, sp = 2;
-    expand(t.y0 - 1, sm);
-    expand(t.y0, s0);
+    R mnext[kMPlanes];
+    load_row(t.y0 - 1, mnext);
+    expand(t.y0 - 1, sm, mnext);
+    load_row(t.y0, mnext);
+    expand(t.y0, s0, mnext);
+    load_row(t.y0 + 1, mnext);
     for (int y = t.y0; y < t.y1; ++y) {
-        expand(y + 1, sp);
+        R mcur[kMPlanes];
+#pragma unroll
+        for (int q = 0; q < kMPlanes; ++q) mcur[q] = mnext[q];
+        if (y + 2 <= t.y1) load_row(y + 2, mnext);
+        expand(y + 1, sp, mcur);
         __syncthreads();
         const bool wall_row = (wallS && y == 0) || (wallN && y == k.ny - 1);
         if (!wall_row) {
@@ -272,7 +296,7 @@ __global__ void k_init_m(const __grid_constant__ KConst<R> k, R* __restrict__ ds
 
 template <class R>
 size_t moment_smem_bytes() {
-    return (size_t)3 * NPLANES * kMBlock * sizeof(R);
+    return (size_t)kMRing * NPLANES * kMBlock * sizeof(R);
 }
 
 // The ring exceeds the default 48 KB of dynamic shared memory in FP64.
@@ -314,7 +338,9 @@ dim3 moment_grid(const KConst<R>& k, int segments) {
 
 template <class R>
 int moment_segments_default(const KConst<R>& k) {
-    // one wave: resident blocks over the bands, rows per segment >= 3
+    // about three waves of resident blocks (measured at 2048^2: one wave of
+    // long segments 45.9 GLUPS, three waves 48.3, six 46.2), rows per
+    // segment >= 3 (moment_grid clamps)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -324,7 +350,7 @@ int moment_segments_default(const KConst<R>& k) {
                                                       moment_smem_bytes<R>());
     if (per_sm < 1) per_sm = 1;
     const int nb = (k.nx + kMBand - 1) / kMBand;
-    int ns = (sms * per_sm) / nb;
+    int ns = 3 * (sms * per_sm) / nb;
     return ns < 1 ? 1 : ns;
 }
 

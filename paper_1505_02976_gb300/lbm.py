@@ -31,7 +31,7 @@ EXPORTED = ("lbm_params_default", "lbm_derived", "lbm_workspace_size", "lbm_crea
             "lbm_batch_autotune", "lbm_batch_set_launch", "lbm_batch_sync", "lbm_batch_nusselt",
             "lbm_batch_moments", "lbm_batch_steps_done", "lbm_batch_kernel_launches",
             "lbm_adjoint", "lbm_totals", "lbm_checkpoint", "lbm_set_force_profile",
-            "lbm_stream_function")
+            "lbm_stream_function", "lbm_set_moment_segments")
 BATCH_MODE = {"fused": 0, "graph": 1, "per_case": 2}
 
 
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True):
     L.lbm_checkpoint.argtypes = [H, C.c_char_p, C.c_int]
     L.lbm_set_force_profile.argtypes = [H, C.c_void_p]
     L.lbm_stream_function.argtypes = [H, C.c_void_p, C.c_int, C.c_void_p]
+    L.lbm_set_moment_segments.argtypes = [H, C.c_int32]
     B = C.c_void_p
     L.lbm_batch_workspace_size.argtypes = [P, C.c_int32, C.POINTER(C.c_size_t)]
     L.lbm_batch_create.argtypes = [P, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(B)]
@@ -289,6 +290,10 @@ class Lattice:
         rng = np.empty(2)
         _check(self.lib.lbm_stream_function(self.h, _ptr(psi), 0, _ptr(rng)), self.h)
         return psi, (float(rng[0]), float(rng[1]))
+
+    def set_moment_segments(self, segments: int = 0):
+        """Row segments per band of the moment-state step (0: default)."""
+        _check(self.lib.lbm_set_moment_segments(self.h, int(segments)), self.h)
 
     def set_force_profile(self, ay=None):
         """Per-row external acceleration a_y(y) (None removes it)."""
