@@ -1,0 +1,303 @@
+// lbm_diag.cu -- kernels off the step's hot path: initial and stored state
+// conversion, moments, Nusselt numbers, residual, totals, stream function.
+// Reductions are deterministic (fixed-order block sums in FP64).
+#include <math.h>
+
+#include "lbm_diag.cuh"
+
+namespace lbm {
+
+constexpr int kResBlock = 128;
+
+template <class R, class S>
+__global__ void k_moments(const __grid_constant__ KConst<R> k, const S* __restrict__ src,
+                          double* __restrict__ p, double* __restrict__ ux, double* __restrict__ uy,
+                          double* __restrict__ T) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= k.nx) return;
+    const State<R> s = node_state_at(k, src, x, y);
+    const long long c = (long long)y * k.nx + x;
+    p[c] = double(s.p);
+    ux[c] = double(s.ux);
+    uy[c] = double(s.uy);
+    T[c] = double(k.T0) + double(s.th);
+}
+
+template <class R, class S>
+__global__ void k_get_state(const __grid_constant__ KConst<R> k, const S* __restrict__ src,
+                            double* __restrict__ f, double* __restrict__ g, double sT0) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= k.nx) return;
+    const long long at = (long long)y * k.pitch + x;
+    const long long c = (long long)y * k.nx + x;
+    const long long N = (long long)k.nx * k.ny;
+    f[c] = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) f[i * N + c] = double(load_pop<S, R>(src + (long long)(i - 1) * k.plane + at, k.scale));
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        g[i * N + c] = double(load_pop<S, R>(src + (long long)(8 + i) * k.plane + at, k.scale)) + w_of<double>(i) * sT0;
+}
+
+template <class R, class S>
+__global__ void k_set_state(const __grid_constant__ KConst<R> k, S* __restrict__ dst,
+                            const double* __restrict__ f, const double* __restrict__ g, double sT0) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= k.nx) return;
+    const long long at = (long long)y * k.pitch + x;
+    const long long c = (long long)y * k.nx + x;
+    const long long N = (long long)k.nx * k.ny;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) store_pop<S, R>(dst + (long long)(i - 1) * k.plane + at, R(f[i * N + c]), k.scale);
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        store_pop<S, R>(dst + (long long)(8 + i) * k.plane + at, R(g[i * N + c] - w_of<double>(i) * sT0), k.scale);
+}
+
+template <class R, class S>
+__global__ void k_nusselt_local(const __grid_constant__ KConst<R> k, const DiagConst d,
+                                const S* __restrict__ src, int side, double* __restrict__ nu) {
+    const int n = side <= SE ? k.ny : k.nx;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double t[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        int x, y;
+        if (side == SW) { x = m; y = j; }
+        else if (side == SE) { x = k.nx - 1 - m; y = j; }
+        else if (side == SS) { x = j; y = m; }
+        else { x = j; y = k.ny - 1 - m; }
+        t[m] = node_T(k, d, src, x, y);
+    }
+    // derivative from the wall inward, then along +x (W, E) or +y (S, N)
+    const double d_in = (-3.0 * t[0] + 4.0 * t[1] - t[2]) * 0.5;
+    const double d_axis = (side == SW || side == SS) ? d_in : -d_in;
+    nu[j] = -d.L * d_axis / d.dT;
+}
+
+__global__ void k_nusselt_mean(const double* __restrict__ nu, int n, double* __restrict__ out) {
+    __shared__ double sh[kReduceBlock / 32];
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < n; j += kReduceBlock) acc += ((j == 0 || j == n - 1) ? 0.5 : 1.0) * nu[j];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[0] = s / double(n - 1);
+}
+
+template <class R, class S>
+__global__ void __launch_bounds__(kResBlock)
+k_residual(const __grid_constant__ KConst<R> k, const S* __restrict__ src, double* __restrict__ snap,
+           double* __restrict__ partial) {
+    __shared__ double sh[kResBlock / 32];
+    const int x = blockIdx.x * kResBlock + threadIdx.x;
+    const int y = blockIdx.y;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (x < k.nx) {
+        const State<R> s = node_state_at(k, src, x, y);
+        const long long N = (long long)k.nx * k.ny;
+        const long long c = (long long)y * k.nx + x;
+        const double ux = double(s.ux), uy = double(s.uy), T = double(k.T0) + double(s.th);
+        const double dx = ux - snap[c], dy = uy - snap[N + c], dT = T - snap[2 * N + c];
+        // the per-node norms in the lattice's arithmetic (FP64 square roots
+        // are slow; the sums stay FP64)
+        const R rx = R(dx), ry = R(dy);
+        v[0] = double(sqrt(rx * rx + ry * ry));
+        v[1] = double(sqrt(s.ux * s.ux + s.uy * s.uy));
+        v[2] = fabs(dT);
+        v[3] = fabs(T);
+        snap[c] = ux;
+        snap[N + c] = uy;
+        snap[2 * N + c] = T;
+    }
+    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const double s = block_sum(v[m], sh);
+        if (threadIdx.x == 0) partial[4 * b + m] = s;
+    }
+}
+
+// Per-block sums of sum_{i=1..8} f_i and sum_i g_i over the stored state.
+template <class R, class S>
+__global__ void __launch_bounds__(kResBlock)
+k_totals(const __grid_constant__ KConst<R> k, const S* __restrict__ src, double sT0, double* __restrict__ partial) {
+    __shared__ double sh[kResBlock / 32];
+    const int x = blockIdx.x * kResBlock + threadIdx.x;
+    const int y = blockIdx.y;
+    double sf = 0.0, sg = 0.0;
+    if (x < k.nx) {
+        const long long at = (long long)y * k.pitch + x;
+        for (int i = 1; i < 9; ++i) sf += double(load_pop<S, R>(src + (long long)(i - 1) * k.plane + at, k.scale));
+        for (int i = 0; i < 9; ++i) sg += double(load_pop<S, R>(src + (long long)(8 + i) * k.plane + at, k.scale));
+        sg += sT0;  // sum_i w_i sigma T0
+    }
+    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    const double a = block_sum(sf, sh);
+    if (threadIdx.x == 0) partial[4 * b + 0] = a;
+    const double c = block_sum(sg, sh);
+    if (threadIdx.x == 0) {
+        partial[4 * b + 1] = c;
+        partial[4 * b + 2] = 0.0;
+        partial[4 * b + 3] = 0.0;
+    }
+}
+
+__global__ void k_reduce4(const double* __restrict__ partial, long long nb, double* __restrict__ out) {
+    __shared__ double sh[kReduceBlock / 32];
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long b = threadIdx.x; b < nb; b += kReduceBlock)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) a[m] += partial[4 * b + m];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const double s = block_sum(a[m], sh);
+        if (threadIdx.x == 0) out[m] = s;
+    }
+}
+
+// Stream function up each column x: psi(x, 0) = 0 and
+// psi(x, y) = psi(x, y - 1) + (u_x(x, y - 1) + u_x(x, y)) / 2, the trapezoid
+// rule for u_x = d psi / dy.  One thread per column; rows are coalesced.
+__global__ void k_stream_function(const double* __restrict__ ux, int nx, int ny, double* __restrict__ psi) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    double s = 0.0;
+    psi[x] = 0.0;
+    for (int y = 1; y < ny; ++y) {
+        s = s + 0.5 * (ux[(long long)(y - 1) * nx + x] + ux[(long long)y * nx + x]);
+        psi[(long long)y * nx + x] = s;
+    }
+}
+
+// out[0] = min, out[1] = max of v[0 .. n-1] (one block; order-independent).
+__global__ void k_minmax(const double* __restrict__ v, long long n, double* __restrict__ out) {
+    __shared__ double lo_s[kReduceBlock / 32], hi_s[kReduceBlock / 32];
+    double lo = INFINITY, hi = -INFINITY;
+    for (long long i = threadIdx.x; i < n; i += kReduceBlock) {
+        lo = fmin(lo, v[i]);
+        hi = fmax(hi, v[i]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        lo_s[wid] = lo;
+        hi_s[wid] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < kReduceBlock / 32; ++i) {
+            lo = fmin(lo, lo_s[i]);
+            hi = fmax(hi, hi_s[i]);
+        }
+        out[0] = lo;
+        out[1] = hi;
+    }
+}
+
+template <class R>
+__global__ void k_convert(const double* __restrict__ in, R* __restrict__ out, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = R(in[i]);
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <class R>
+cudaError_t launch_convert(const double* in, R* out, long long n, cudaStream_t st) {
+    k_convert<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+template cudaError_t launch_convert<double>(const double*, double*, long long, cudaStream_t);
+template cudaError_t launch_convert<float>(const double*, float*, long long, cudaStream_t);
+
+cudaError_t launch_stream_function(const double* ux, int nx, int ny, double* psi, double* range,
+                                   cudaStream_t st) {
+    k_stream_function<<<(nx + 127) / 128, 128, 0, st>>>(ux, nx, ny, psi);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_minmax<<<1, kReduceBlock, 0, st>>>(psi, (long long)nx * ny, range);
+    return cudaGetLastError();
+}
+
+long long residual_blocks(int nx, int ny) {
+    return (long long)((nx + kResBlock - 1) / kResBlock) * ny;
+}
+
+template <class R, class S>
+cudaError_t launch_moments(const KConst<R>& k, const S* src, double* p, double* ux, double* uy,
+                           double* T, cudaStream_t st) {
+    k_moments<R, S><<<row_grid(k.nx, k.ny, 128), 128, 0, st>>>(k, src, p, ux, uy, T);
+    return cudaGetLastError();
+}
+
+template <class R, class S>
+cudaError_t launch_get_state(const KConst<R>& k, const S* src, double* f, double* g, double sT0,
+                             cudaStream_t st) {
+    k_get_state<R, S><<<row_grid(k.nx, k.ny, 128), 128, 0, st>>>(k, src, f, g, sT0);
+    return cudaGetLastError();
+}
+
+template <class R, class S>
+cudaError_t launch_set_state(const KConst<R>& k, S* dst, const double* f, const double* g,
+                             double sT0, cudaStream_t st) {
+    k_set_state<R, S><<<row_grid(k.nx, k.ny, 128), 128, 0, st>>>(k, dst, f, g, sT0);
+    return cudaGetLastError();
+}
+
+template <class R, class S>
+cudaError_t launch_nusselt(const KConst<R>& k, const DiagConst& d, const S* src, int side,
+                           double* nu_local, double* out, cudaStream_t st) {
+    const int n = side <= SE ? k.ny : k.nx;
+    k_nusselt_local<R, S><<<(n + 127) / 128, 128, 0, st>>>(k, d, src, side, nu_local);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_nusselt_mean<<<1, kReduceBlock, 0, st>>>(nu_local, n, out);
+    return cudaGetLastError();
+}
+
+template <class R, class S>
+cudaError_t launch_residual(const KConst<R>& k, const S* src, double* snap, double* partial,
+                            double* out, cudaStream_t st) {
+    k_residual<R, S><<<row_grid(k.nx, k.ny, kResBlock), kResBlock, 0, st>>>(k, src, snap, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce4<<<1, kReduceBlock, 0, st>>>(partial, residual_blocks(k.nx, k.ny), out);
+    return cudaGetLastError();
+}
+
+template <class R, class S>
+cudaError_t launch_totals(const KConst<R>& k, const S* src, double sT0, double* partial, double* out,
+                          cudaStream_t st) {
+    k_totals<R, S><<<row_grid(k.nx, k.ny, kResBlock), kResBlock, 0, st>>>(k, src, sT0, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce4<<<1, kReduceBlock, 0, st>>>(partial, residual_blocks(k.nx, k.ny), out);
+    return cudaGetLastError();
+}
+
+#define LBM_INSTANTIATE_DIAG(R, S)                                                                        \
+    template cudaError_t launch_totals<R, S>(const KConst<R>&, const S*, double, double*, double*,  \
+                                             cudaStream_t);                                         \
+    template cudaError_t launch_moments<R, S>(const KConst<R>&, const S*, double*, double*, double*, \
+                                              double*, cudaStream_t);                               \
+    template cudaError_t launch_get_state<R, S>(const KConst<R>&, const S*, double*, double*,       \
+                                                double, cudaStream_t);                              \
+    template cudaError_t launch_set_state<R, S>(const KConst<R>&, S*, const double*, const double*, \
+                                                double, cudaStream_t);                              \
+    template cudaError_t launch_nusselt<R, S>(const KConst<R>&, const DiagConst&, const S*, int,    \
+                                              double*, double*, cudaStream_t);                      \
+    template cudaError_t launch_residual<R, S>(const KConst<R>&, const S*, double*, double*,        \
+                                               double*, cudaStream_t);
+
+LBM_INSTANTIATE_DIAG(double, double)
+LBM_INSTANTIATE_DIAG(float, float)
+LBM_INSTANTIATE_DIAG(float, __half)
+
+}  // namespace lbm
