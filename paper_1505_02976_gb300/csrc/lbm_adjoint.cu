@@ -8,10 +8,17 @@
 // on the porosity at the source and at x, and on the Dirichlet T_b.  The
 // adjoint runs the steps backwards:
 //   k_adj_local:  per node, the transposed Jacobian of its update applied to
-//                 lambda_{n+1}(x) -- 17 + 4 directional derivatives of the very
+//                 lambda_{n+1}(x), from directional derivatives of the very
 //                 same per-node code (node_update_generic) evaluated in dual
-//                 numbers -- giving the adjoints of the pulled values and
-//                 the porosity / wall-temperature contributions;
+//                 numbers, giving the adjoints of the pulled values and the
+//                 porosity / wall-temperature contributions.  The update
+//                 depends on its 17 pulled values only through the BGK term
+//                 (1 - 1/tau) in and through nine linear moment sums M in
+//                 (Sec. 3.1-3.3: sum g, c g, sum f, c f, c c f), so
+//                 J = diag(1 - 1/tau) + D M and J^T l = diag(1 - 1/tau) l +
+//                 M^T D^T l: nine derivatives along directions d_k with
+//                 M d_k = e_k give D^T l (plus up to two for the porosity
+//                 and wall temperature);
 //   k_adj_gather: the transpose of pull streaming: each stored value
 //                 collects the adjoints of every node that pulled it (its
 //                 downstream neighbour, the wall nodes whose x_f or x_ff it
@@ -36,9 +43,53 @@ constexpr int kAdjBlock = 128;
 template <class R>
 __device__ __forceinline__ long long at_of(const KConst<R>& k, int x, int y) { return (long long)y * k.pitch + x; }
 
-// Seeds of the local transposed Jacobian: 0..16 pulled populations (f_1..f_8,
-// h_0..h_8), 17 porosity at the source node, 18 porosity at the node (wall
-// nodes only), 19 T(x_ff) (adiabatic walls), 20 the Dirichlet T_b.
+// Directions d_k in the space of the 17 pulled values (f_1..f_8, h_0..h_8)
+// with M d_k = e_k for the moment sums k = 0 sum h, 1 sum_x c_x h,
+// 2 sum c_y h, 3 sum f, 4 sum c_x f, 5 sum c_y f, 6 sum c_x^2 f,
+// 7 sum c_y^2 f, 8 sum c_x c_y f (M: row k holds the weights of sum k).
+__device__ __forceinline__ float moment_dir(int k, int q) {
+    if (q >= 8) {
+        const int i = q - 8;
+        if (k == 0) return i == 0 ? 1.f : 0.f;
+        if (k == 1) return i == 1 ? 0.5f : (i == 3 ? -0.5f : 0.f);
+        if (k == 2) return i == 2 ? 0.5f : (i == 4 ? -0.5f : 0.f);
+        return 0.f;
+    }
+    const int i = q + 1;
+    const bool axis13 = i == 1 || i == 3, axis24 = i == 2 || i == 4, diag = i >= 5;
+    switch (k) {
+    case 3: return axis13 || axis24 ? 0.5f : -0.25f;            // sum f
+    case 4: return i == 1 ? 0.5f : (i == 3 ? -0.5f : 0.f);      // sum c_x f
+    case 5: return i == 2 ? 0.5f : (i == 4 ? -0.5f : 0.f);      // sum c_y f
+    case 6: return axis24 ? -0.5f : (diag ? 0.25f : 0.f);       // sum c_x^2 f
+    case 7: return axis13 ? -0.5f : (diag ? 0.25f : 0.f);       // sum c_y^2 f
+    case 8: return diag ? ((i == 5 || i == 7) ? 0.25f : -0.25f) : 0.f;  // sum c_x c_y f
+    default: return 0.f;
+    }
+}
+
+// Weight of pulled value q in moment sum k (row k of M).
+__device__ __forceinline__ float moment_weight(int k, int q) {
+    if (q >= 8) {
+        const int i = q - 8;
+        return k == 0 ? 1.f : (k == 1 ? float(cx_of(i)) : (k == 2 ? float(cy_of(i)) : 0.f));
+    }
+    const int i = q + 1;
+    const float cx = float(cx_of(i)), cy = float(cy_of(i));
+    switch (k) {
+    case 3: return 1.f;
+    case 4: return cx;
+    case 5: return cy;
+    case 6: return cx * cx;
+    case 7: return cy * cy;
+    case 8: return cx * cy;
+    default: return 0.f;
+    }
+}
+
+// Passes of the local transposed Jacobian: 0..8 the moment directions d_k,
+// 9 porosity at the source node, 10 porosity at the node (wall nodes only),
+// 11 T(x_ff) (adiabatic walls), 12 the Dirichlet T_b.
 template <class R, class S>
 __global__ void __launch_bounds__(kAdjBlock)
 k_adj_local(const __grid_constant__ KConst<R> k, const S* __restrict__ state, const R* __restrict__ lam,
@@ -65,35 +116,50 @@ k_adj_local(const __grid_constant__ KConst<R> k, const S* __restrict__ state, co
 #pragma unroll
     for (int q = 0; q < 17; ++q) l[q] = lam[q * k.plane + a];
 
-    R vin[17];
+    // (D^T l)_k = l . J d_k - l . (diag(1 - 1/tau) d_k)
+    R dtl[9];
     R v_es = R(0), v_ex = R(0), v_ff = R(0), v_tb = R(0);
     const bool field = k.eps_field != nullptr;
 #pragma unroll 1
-    for (int j = 0; j < 21; ++j) {
-        if (j == 17 && !field) continue;
-        if (j == 18 && (!field || !w.wall)) continue;
-        if (j == 19 && !(w.wall && w.tside < 0)) continue;
-        if (j == 20 && !(w.wall && w.tside >= 0)) continue;
+    for (int j = 0; j < 13; ++j) {
+        if (j == 9 && !field) continue;
+        if (j == 10 && (!field || !w.wall)) continue;
+        if (j == 11 && !(w.wall && w.tside < 0)) continue;
+        if (j == 12 && !(w.wall && w.tside >= 0)) continue;
         Dual<R> din[17], dout[17];
 #pragma unroll
-        for (int q = 0; q < 17; ++q) din[q] = Dual<R>(in[q], q == j ? R(1) : R(0));
-        const Dual<R> des(eps_s, j == 17 ? R(1) : R(0));
+        for (int q = 0; q < 17; ++q) din[q] = Dual<R>(in[q], j < 9 ? R(moment_dir(j, q)) : R(0));
+        const Dual<R> des(eps_s, j == 9 ? R(1) : R(0));
         // an interior node's own porosity is its source porosity
-        const Dual<R> dex = w.wall ? Dual<R>(eps_x, j == 18 ? R(1) : R(0)) : des;
-        const Dual<R> dff(thff, j == 19 ? R(1) : R(0));
-        const Dual<R> dtb(thb, j == 20 ? R(1) : R(0));
+        const Dual<R> dex = w.wall ? Dual<R>(eps_x, j == 10 ? R(1) : R(0)) : des;
+        const Dual<R> dff(thff, j == 11 ? R(1) : R(0));
+        const Dual<R> dtb(thb, j == 12 ? R(1) : R(0));
         node_update_generic(k, w, din, des, dex, dff, dtb, row_ay(k, ys), row_ay(k, y), dout);
         R acc = R(0);
 #pragma unroll
         for (int q = 0; q < 17; ++q) acc += dout[q].d * l[q];
-        if (j < 17) vin[j] = acc;
-        else if (j == 17) v_es = acc;
-        else if (j == 18) v_ex = acc;
-        else if (j == 19) v_ff = acc;
-        else v_tb = acc;
-    }
+        if (j < 9) {
 #pragma unroll
-    for (int q = 0; q < 17; ++q) V[q * k.plane + a] = vin[q];
+            for (int q = 0; q < 17; ++q) acc -= (q < 8 ? k.omf : k.omT) * l[q] * R(moment_dir(j, q));
+            dtl[j] = acc;
+        } else if (j == 9) {
+            v_es = acc;
+        } else if (j == 10) {
+            v_ex = acc;
+        } else if (j == 11) {
+            v_ff = acc;
+        } else {
+            v_tb = acc;
+        }
+    }
+    // V = J^T l = diag(1 - 1/tau) l + M^T D^T l
+#pragma unroll
+    for (int q = 0; q < 17; ++q) {
+        R v = (q < 8 ? k.omf : k.omT) * l[q];
+#pragma unroll
+        for (int m = 0; m < 9; ++m) v += R(moment_weight(m, q)) * dtl[m];
+        V[q * k.plane + a] = v;
+    }
     Vff[a] = v_ff;
     const long long c = (long long)y * k.nx + x;
     if (!w.wall) {

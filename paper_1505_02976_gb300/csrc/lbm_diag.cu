@@ -96,16 +96,17 @@ k_residual(const __grid_constant__ KConst<R> k, const S* __restrict__ src, doubl
     const int y = blockIdx.y;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (x < k.nx) {
-        const State<R> s = node_state_at(k, src, x, y);
+        R rux, ruy, rth;
+        node_u_th(k, src, x, y, &rux, &ruy, &rth);
         const long long N = (long long)k.nx * k.ny;
         const long long c = (long long)y * k.nx + x;
-        const double ux = double(s.ux), uy = double(s.uy), T = double(k.T0) + double(s.th);
+        const double ux = double(rux), uy = double(ruy), T = double(k.T0) + double(rth);
         const double dx = ux - snap[c], dy = uy - snap[N + c], dT = T - snap[2 * N + c];
         // the per-node norms in the lattice's arithmetic (FP64 square roots
         // are slow; the sums stay FP64)
         const R rx = R(dx), ry = R(dy);
         v[0] = double(sqrt(rx * rx + ry * ry));
-        v[1] = double(sqrt(s.ux * s.ux + s.uy * s.uy));
+        v[1] = double(sqrt(rux * rux + ruy * ruy));
         v[2] = fabs(dT);
         v[3] = fabs(T);
         snap[c] = ux;

@@ -26,6 +26,34 @@ __device__ __forceinline__ State<R> node_state_at(const KConst<R>& k, const S* _
     return wall_state(k, cb, w, s, thff, thb);
 }
 
+// (u_x, u_y, T - T0) of node (x, y) after streaming: the step's fast path
+// for interior nodes (same moments as node_state_at up to rounding order),
+// node_state_at for wall nodes.
+template <class R, class S>
+__device__ __forceinline__ void node_u_th(const KConst<R>& k, const S* __restrict__ src, int x, int y, R* ux,
+                                          R* uy, R* th) {
+    if (is_wall(k, x, y)) {
+        const State<R> s = node_state_at(k, src, x, y);
+        *ux = s.ux;
+        *uy = s.uy;
+        *th = s.th;
+        return;
+    }
+    Pops<R> P;
+    pull(k, src, x, y, P);
+    FastState<R> s;
+    if (k.eps_field) {
+        KConst<R> kc = k;
+        apply_eps(kc, node_eps(k, x, y));
+        s = fast_moments(kc, P.f, P.h, y);
+    } else {
+        s = fast_moments(k, P.f, P.h, y);
+    }
+    *ux = s.ux;
+    *uy = s.uy;
+    *th = s.th;
+}
+
 // T of node (x, y) in FP64 from the stored populations, with the wall rules
 // of Sec. 3.4 (Dirichlet value, or Eq. TNEESApGra on adiabatic walls).
 template <class R, class S>
