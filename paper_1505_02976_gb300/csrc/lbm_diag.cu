@@ -7,7 +7,12 @@
 
 namespace lbm {
 
-constexpr int kResBlock = 128;
+// Residual and totals: a fixed grid of at most kResGrid blocks strides over
+// the nodes in a fixed order (deterministic), so that the FP64 work per
+// node is a few additions (FP64 arithmetic is slow on this GPU) and the
+// final reduction reads few partials.
+constexpr int kResBlock = 256;
+constexpr int kResGrid = 1024;
 
 template <class R, class S>
 __global__ void k_moments(const __grid_constant__ KConst<R> k, const S* __restrict__ src,
@@ -87,62 +92,61 @@ __global__ void k_nusselt_mean(const double* __restrict__ nu, int n, double* __r
     if (threadIdx.x == 0) out[0] = s / double(n - 1);
 }
 
+// Per-node terms in the lattice's arithmetic R (the snapshot holds values
+// of type R, so the differences are exact up to one rounding); per-thread
+// sums in R over the thread's nodes, block and grid sums in FP64.
 template <class R, class S>
 __global__ void __launch_bounds__(kResBlock)
 k_residual(const __grid_constant__ KConst<R> k, const S* __restrict__ src, double* __restrict__ snap,
            double* __restrict__ partial) {
     __shared__ double sh[kResBlock / 32];
-    const int x = blockIdx.x * kResBlock + threadIdx.x;
-    const int y = blockIdx.y;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (x < k.nx) {
-        R rux, ruy, rth;
-        node_u_th(k, src, x, y, &rux, &ruy, &rth);
-        const long long N = (long long)k.nx * k.ny;
-        const long long c = (long long)y * k.nx + x;
-        const double ux = double(rux), uy = double(ruy), T = double(k.T0) + double(rth);
-        const double dx = ux - snap[c], dy = uy - snap[N + c], dT = T - snap[2 * N + c];
-        // the per-node norms in the lattice's arithmetic (FP64 square roots
-        // are slow; the sums stay FP64)
-        const R rx = R(dx), ry = R(dy);
-        v[0] = double(sqrt(rx * rx + ry * ry));
-        v[1] = double(sqrt(rux * rux + ruy * ruy));
-        v[2] = fabs(dT);
-        v[3] = fabs(T);
-        snap[c] = ux;
-        snap[N + c] = uy;
-        snap[2 * N + c] = T;
+    const long long N = (long long)k.nx * k.ny;
+    R v[4] = {R(0), R(0), R(0), R(0)};
+    for (long long c = (long long)blockIdx.x * kResBlock + threadIdx.x; c < N; c += (long long)gridDim.x * kResBlock) {
+        const int y = (int)(c / k.nx), x = (int)(c - (long long)y * k.nx);
+        R ux, uy, th;
+        node_u_th(k, src, x, y, &ux, &uy, &th);
+        const R T = k.T0 + th;
+        const R dx = ux - R(snap[c]), dy = uy - R(snap[N + c]), dT = T - R(snap[2 * N + c]);
+        v[0] += sqrt(dx * dx + dy * dy);
+        v[1] += sqrt(ux * ux + uy * uy);
+        v[2] += fabs(dT);
+        v[3] += fabs(T);
+        snap[c] = double(ux);
+        snap[N + c] = double(uy);
+        snap[2 * N + c] = double(T);
     }
-    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        const double s = block_sum(v[m], sh);
-        if (threadIdx.x == 0) partial[4 * b + m] = s;
+        const double s = block_sum(double(v[m]), sh);
+        if (threadIdx.x == 0) partial[4 * blockIdx.x + m] = s;
     }
 }
 
 // Per-block sums of sum_{i=1..8} f_i and sum_i g_i over the stored state.
+// Per node: the sums of its populations in R; per thread and above: FP64.
 template <class R, class S>
 __global__ void __launch_bounds__(kResBlock)
 k_totals(const __grid_constant__ KConst<R> k, const S* __restrict__ src, double sT0, double* __restrict__ partial) {
     __shared__ double sh[kResBlock / 32];
-    const int x = blockIdx.x * kResBlock + threadIdx.x;
-    const int y = blockIdx.y;
+    const long long N = (long long)k.nx * k.ny;
     double sf = 0.0, sg = 0.0;
-    if (x < k.nx) {
+    for (long long c = (long long)blockIdx.x * kResBlock + threadIdx.x; c < N; c += (long long)gridDim.x * kResBlock) {
+        const int y = (int)(c / k.nx), x = (int)(c - (long long)y * k.nx);
         const long long at = (long long)y * k.pitch + x;
-        for (int i = 1; i < 9; ++i) sf += double(load_pop<S, R>(src + (long long)(i - 1) * k.plane + at, k.scale));
-        for (int i = 0; i < 9; ++i) sg += double(load_pop<S, R>(src + (long long)(8 + i) * k.plane + at, k.scale));
-        sg += sT0;  // sum_i w_i sigma T0
+        R nf = R(0), ng = R(0);
+        for (int i = 1; i < 9; ++i) nf += load_pop<S, R>(src + (long long)(i - 1) * k.plane + at, k.scale);
+        for (int i = 0; i < 9; ++i) ng += load_pop<S, R>(src + (long long)(8 + i) * k.plane + at, k.scale);
+        sf += double(nf);
+        sg += double(ng) + sT0;  // sum_i w_i sigma T0 of the stored deviations
     }
-    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
     const double a = block_sum(sf, sh);
-    if (threadIdx.x == 0) partial[4 * b + 0] = a;
-    const double c = block_sum(sg, sh);
+    if (threadIdx.x == 0) partial[4 * blockIdx.x + 0] = a;
+    const double b = block_sum(sg, sh);
     if (threadIdx.x == 0) {
-        partial[4 * b + 1] = c;
-        partial[4 * b + 2] = 0.0;
-        partial[4 * b + 3] = 0.0;
+        partial[4 * blockIdx.x + 1] = b;
+        partial[4 * blockIdx.x + 2] = 0.0;
+        partial[4 * blockIdx.x + 3] = 0.0;
     }
 }
 
@@ -228,7 +232,8 @@ cudaError_t launch_stream_function(const double* ux, int nx, int ny, double* psi
 }
 
 long long residual_blocks(int nx, int ny) {
-    return (long long)((nx + kResBlock - 1) / kResBlock) * ny;
+    const long long b = ((long long)nx * ny + kResBlock - 1) / kResBlock;
+    return b < kResGrid ? b : kResGrid;
 }
 
 template <class R, class S>
@@ -266,7 +271,7 @@ cudaError_t launch_nusselt(const KConst<R>& k, const DiagConst& d, const S* src,
 template <class R, class S>
 cudaError_t launch_residual(const KConst<R>& k, const S* src, double* snap, double* partial,
                             double* out, cudaStream_t st) {
-    k_residual<R, S><<<row_grid(k.nx, k.ny, kResBlock), kResBlock, 0, st>>>(k, src, snap, partial);
+    k_residual<R, S><<<(unsigned)residual_blocks(k.nx, k.ny), kResBlock, 0, st>>>(k, src, snap, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce4<<<1, kReduceBlock, 0, st>>>(partial, residual_blocks(k.nx, k.ny), out);
@@ -276,7 +281,7 @@ cudaError_t launch_residual(const KConst<R>& k, const S* src, double* snap, doub
 template <class R, class S>
 cudaError_t launch_totals(const KConst<R>& k, const S* src, double sT0, double* partial, double* out,
                           cudaStream_t st) {
-    k_totals<R, S><<<row_grid(k.nx, k.ny, kResBlock), kResBlock, 0, st>>>(k, src, sT0, partial);
+    k_totals<R, S><<<(unsigned)residual_blocks(k.nx, k.ny), kResBlock, 0, st>>>(k, src, sT0, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce4<<<1, kReduceBlock, 0, st>>>(partial, residual_blocks(k.nx, k.ny), out);
