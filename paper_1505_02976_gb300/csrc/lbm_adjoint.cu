@@ -7,8 +7,8 @@
 // node (x itself, or x_f for a wall node), on T(x_ff) for adiabatic walls,
 // on the porosity at the source and at x, and on the Dirichlet T_b.  The
 // adjoint runs the steps backwards:
-//   k_adj_local:  per node, the transposed Jacobian of its update applied to
-//                 lambda_{n+1}(x), from directional derivatives of the very
+//   k_adj_pass,   per node, the transposed Jacobian of its update applied to
+//   k_adj_combine: lambda_{n+1}(x), from directional derivatives of the very
 //                 same per-node code (node_update_generic) evaluated in dual
 //                 numbers, giving the adjoints of the pulled values and the
 //                 porosity / wall-temperature contributions.  The update
@@ -18,7 +18,7 @@
 //                 J = diag(1 - 1/tau) + D M and J^T l = diag(1 - 1/tau) l +
 //                 M^T D^T l: nine derivatives along directions d_k with
 //                 M d_k = e_k give D^T l (plus up to two for the porosity
-//                 and wall temperature);
+//                 and wall temperature), one thread per (node, pass);
 //   k_adj_gather: the transpose of pull streaming: each stored value
 //                 collects the adjoints of every node that pulled it (its
 //                 downstream neighbour, the wall nodes whose x_f or x_ff it
@@ -90,84 +90,87 @@ __device__ __forceinline__ float moment_weight(int k, int q) {
 // Passes of the local transposed Jacobian: 0..8 the moment directions d_k,
 // 9 porosity at the source node, 10 porosity at the node (wall nodes only),
 // 11 T(x_ff) (adiabatic walls), 12 the Dirichlet T_b.
+constexpr int kAdjPasses = 13;
+
+// One pass per thread (blockIdx.z = pass j): the directional derivative of
+// node (x, y)'s update along its direction, dotted with lambda_{n+1}(x).
+// D[j][x]: for j < 9 (D^T l)_j = l . J d_j - l . (diag(1 - 1/tau) d_j);
+// otherwise l . (dout / d input j), 0 where the input does not exist.
 template <class R, class S>
 __global__ void __launch_bounds__(kAdjBlock)
-k_adj_local(const __grid_constant__ KConst<R> k, const S* __restrict__ state, const R* __restrict__ lam,
-            R* __restrict__ V, R* __restrict__ Vff, double* __restrict__ g_eps, double* __restrict__ g_epsf,
-            double* __restrict__ g_tb) {
+k_adj_pass(const __grid_constant__ KConst<R> k, const S* __restrict__ state, const R* __restrict__ lam,
+           R* __restrict__ D) {
     const int x = blockIdx.x * kAdjBlock + threadIdx.x;
     const int y = blockIdx.y;
+    const int j = blockIdx.z;
     if (x >= k.nx) return;
+    const long long a = at_of(k, x, y);
     const WallInfo w = classify(k, x, y);
+    const bool field = k.eps_field != nullptr;
+    const bool used = j < 9 || (j == 9 && field) || (j == 10 && field && w.wall) ||
+                      (j == 11 && w.wall && w.tside < 0) || (j == 12 && w.wall && w.tside >= 0);
+    if (!used) {
+        D[j * k.plane + a] = R(0);
+        return;
+    }
     const int xs = w.wall ? w.xs : x, ys = w.wall ? w.ys : y;
     Pops<R> P;
     pull(k, state, xs, ys, P);
-    R in[17];
-#pragma unroll
-    for (int i = 1; i < 9; ++i) in[i - 1] = P.f[i];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) in[8 + i] = P.h[i];
     R thff = R(0);
     if (w.wall && w.tside < 0) thff = (pull_hsum<R, R, S>(k, state, w.xff, w.yff) + R(0.5) * k.Q) * k.inv_sigma;
     const R thb = (w.wall && w.tside >= 0) ? k.T_bc[w.tside] - k.T0 : R(0);
     const R eps_s = node_eps(k, xs, ys), eps_x = node_eps(k, x, y);
-    const long long a = at_of(k, x, y);
-    R l[17];
+    Dual<R> din[17], dout[17];
 #pragma unroll
-    for (int q = 0; q < 17; ++q) l[q] = lam[q * k.plane + a];
-
-    // (D^T l)_k = l . J d_k - l . (diag(1 - 1/tau) d_k)
-    R dtl[9];
-    R v_es = R(0), v_ex = R(0), v_ff = R(0), v_tb = R(0);
-    const bool field = k.eps_field != nullptr;
-#pragma unroll 1
-    for (int j = 0; j < 13; ++j) {
-        if (j == 9 && !field) continue;
-        if (j == 10 && (!field || !w.wall)) continue;
-        if (j == 11 && !(w.wall && w.tside < 0)) continue;
-        if (j == 12 && !(w.wall && w.tside >= 0)) continue;
-        Dual<R> din[17], dout[17];
+    for (int i = 1; i < 9; ++i) din[i - 1] = Dual<R>(P.f[i], j < 9 ? R(moment_dir(j, i - 1)) : R(0));
 #pragma unroll
-        for (int q = 0; q < 17; ++q) din[q] = Dual<R>(in[q], j < 9 ? R(moment_dir(j, q)) : R(0));
-        const Dual<R> des(eps_s, j == 9 ? R(1) : R(0));
-        // an interior node's own porosity is its source porosity
-        const Dual<R> dex = w.wall ? Dual<R>(eps_x, j == 10 ? R(1) : R(0)) : des;
-        const Dual<R> dff(thff, j == 11 ? R(1) : R(0));
-        const Dual<R> dtb(thb, j == 12 ? R(1) : R(0));
-        node_update_generic(k, w, din, des, dex, dff, dtb, row_ay(k, ys), row_ay(k, y), dout);
-        R acc = R(0);
-#pragma unroll
-        for (int q = 0; q < 17; ++q) acc += dout[q].d * l[q];
-        if (j < 9) {
-#pragma unroll
-            for (int q = 0; q < 17; ++q) acc -= (q < 8 ? k.omf : k.omT) * l[q] * R(moment_dir(j, q));
-            dtl[j] = acc;
-        } else if (j == 9) {
-            v_es = acc;
-        } else if (j == 10) {
-            v_ex = acc;
-        } else if (j == 11) {
-            v_ff = acc;
-        } else {
-            v_tb = acc;
-        }
-    }
-    // V = J^T l = diag(1 - 1/tau) l + M^T D^T l
+    for (int i = 0; i < 9; ++i) din[8 + i] = Dual<R>(P.h[i], j < 9 ? R(moment_dir(j, 8 + i)) : R(0));
+    const Dual<R> des(eps_s, j == 9 ? R(1) : R(0));
+    // an interior node's own porosity is its source porosity
+    const Dual<R> dex = w.wall ? Dual<R>(eps_x, j == 10 ? R(1) : R(0)) : des;
+    const Dual<R> dff(thff, j == 11 ? R(1) : R(0));
+    const Dual<R> dtb(thb, j == 12 ? R(1) : R(0));
+    node_update_generic(k, w, din, des, dex, dff, dtb, row_ay(k, ys), row_ay(k, y), dout);
+    R acc = R(0);
 #pragma unroll
     for (int q = 0; q < 17; ++q) {
-        R v = (q < 8 ? k.omf : k.omT) * l[q];
+        const R l = lam[q * k.plane + a];
+        acc += dout[q].d * l;
+        if (j < 9) acc -= (q < 8 ? k.omf : k.omT) * l * R(moment_dir(j, q));
+    }
+    D[j * k.plane + a] = acc;
+}
+
+// V = J^T l = diag(1 - 1/tau) l + M^T D^T l per node, the x_ff adjoint, and
+// the porosity / wall-temperature gradient contributions.
+template <class R>
+__global__ void __launch_bounds__(kAdjBlock)
+k_adj_combine(const __grid_constant__ KConst<R> k, const R* __restrict__ lam, const R* __restrict__ D,
+              R* __restrict__ V, R* __restrict__ Vff, double* __restrict__ g_eps, double* __restrict__ g_epsf,
+              double* __restrict__ g_tb) {
+    const int x = blockIdx.x * kAdjBlock + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= k.nx) return;
+    const long long a = at_of(k, x, y);
+    R dtl[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) dtl[m] = D[m * k.plane + a];
+#pragma unroll
+    for (int q = 0; q < 17; ++q) {
+        R v = (q < 8 ? k.omf : k.omT) * lam[q * k.plane + a];
 #pragma unroll
         for (int m = 0; m < 9; ++m) v += R(moment_weight(m, q)) * dtl[m];
         V[q * k.plane + a] = v;
     }
-    Vff[a] = v_ff;
+    Vff[a] = D[11 * k.plane + a];
     const long long c = (long long)y * k.nx + x;
-    if (!w.wall) {
+    const R v_es = D[9 * k.plane + a];
+    if (!classify(k, x, y).wall) {
         g_eps[c] += double(v_es);
     } else {
-        g_eps[c] += double(v_ex);
+        g_eps[c] += double(D[10 * k.plane + a]);
         g_epsf[c] += double(v_es);
-        g_tb[c] += double(v_tb);
+        g_tb[c] += double(D[12 * k.plane + a]);
     }
 }
 
@@ -240,11 +243,15 @@ __global__ void k_adj_seed(const __grid_constant__ KConst<R> k, const double* __
     }
 }
 
+// D: scratch of kAdjPasses planes.
 template <class R, class S>
-cudaError_t launch_adj_local(const KConst<R>& k, const S* state, const R* lam, R* V, R* Vff, double* g_eps,
+cudaError_t launch_adj_local(const KConst<R>& k, const S* state, const R* lam, R* D, R* V, R* Vff, double* g_eps,
                              double* g_epsf, double* g_tb, cudaStream_t st) {
-    const dim3 grid((unsigned)((k.nx + kAdjBlock - 1) / kAdjBlock), (unsigned)k.ny);
-    k_adj_local<R, S><<<grid, kAdjBlock, 0, st>>>(k, state, lam, V, Vff, g_eps, g_epsf, g_tb);
+    const unsigned bx = (unsigned)((k.nx + kAdjBlock - 1) / kAdjBlock);
+    k_adj_pass<R, S><<<dim3(bx, (unsigned)k.ny, kAdjPasses), kAdjBlock, 0, st>>>(k, state, lam, D);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_adj_combine<R><<<dim3(bx, (unsigned)k.ny), kAdjBlock, 0, st>>>(k, lam, D, V, Vff, g_eps, g_epsf, g_tb);
     return cudaGetLastError();
 }
 
@@ -325,8 +332,9 @@ lbm_status run_adjoint(lbm_handle* h, const lbm::KConst<R>& k, int64_t n, int64_
     R* lam1 = (R*)alloc(lam_bytes);
     R* V = (R*)alloc(lam_bytes);
     R* Vff = (R*)alloc((size_t)k.plane * sizeof(R));
+    R* Dp = (R*)alloc((size_t)lbm::kAdjPasses * k.plane * sizeof(R));  // per-pass products
     double* g = (double*)alloc(4 * N * sizeof(double));  // g_eps, g_epsf, g_tb, dL/dT
-    if (!ckpt || !segs || !lam0 || !lam1 || !V || !Vff || !g)
+    if (!ckpt || !segs || !lam0 || !lam1 || !V || !Vff || !Dp || !g)
         return fail_free(LBM_ERR_OOM, "adjoint buffers (checkpoints grow as sqrt(n))");
     double *g_eps = g, *g_epsf = g + N, *g_tb = g + 2 * N, *dLdT = g + 3 * N;
     if (cudaMemsetAsync(g, 0, 3 * N * sizeof(double), st) != cudaSuccess) return fail_free(LBM_ERR_CUDA, "memset");
@@ -392,7 +400,7 @@ lbm_status run_adjoint(lbm_handle* h, const lbm::KConst<R>& k, int64_t n, int64_
             if (e != cudaSuccess) return fail_free(LBM_ERR_CUDA, "recompute step");
         }
         for (int64_t t = len - 1; t >= 0; --t) {
-            e = lbm::launch_adj_local(k, (const S*)(segs + sb * (size_t)t), lc, V, Vff, g_eps, g_epsf, g_tb, st);
+            e = lbm::launch_adj_local(k, (const S*)(segs + sb * (size_t)t), lc, Dp, V, Vff, g_eps, g_epsf, g_tb, st);
             if (e == cudaSuccess) e = lbm::launch_adj_gather(k, V, Vff, ln, st);
             if (e != cudaSuccess) return fail_free(LBM_ERR_CUDA, std::string("adjoint kernels: ") + cudaGetErrorString(e));
             std::swap(lc, ln);

@@ -8,11 +8,28 @@
 namespace lbm {
 
 // Residual and totals: a fixed grid of at most kResGrid blocks strides over
-// the nodes in a fixed order (deterministic), so that the FP64 work per
-// node is a few additions (FP64 arithmetic is slow on this GPU) and the
-// final reduction reads few partials.
+// the nodes in a fixed order (deterministic).  FP64 arithmetic is slow on
+// this GPU, so the per-node work and the warp sums of the residual run in
+// the lattice's arithmetic and only the per-warp results are added in FP64;
+// the grid is large enough that every node's loads are in flight at once.
 constexpr int kResBlock = 256;
-constexpr int kResGrid = 1024;
+constexpr int kResGrid = 8192;
+
+// Block sum of one value per thread: warp sums in R, then the warps' sums
+// in FP64 in a fixed order (valid in thread 0).
+template <class R>
+__device__ __forceinline__ double block_sum_r(R v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = double(v);
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    return s;
+}
 
 template <class R, class S>
 __global__ void k_moments(const __grid_constant__ KConst<R> k, const S* __restrict__ src,
@@ -103,7 +120,7 @@ k_residual(const __grid_constant__ KConst<R> k, const S* __restrict__ src, doubl
     const long long N = (long long)k.nx * k.ny;
     R v[4] = {R(0), R(0), R(0), R(0)};
     for (long long c = (long long)blockIdx.x * kResBlock + threadIdx.x; c < N; c += (long long)gridDim.x * kResBlock) {
-        const int y = (int)(c / k.nx), x = (int)(c - (long long)y * k.nx);
+        const int y = (int)((unsigned long long)c / (unsigned)k.nx), x = (int)(c - (long long)y * k.nx);
         R ux, uy, th;
         node_u_th(k, src, x, y, &ux, &uy, &th);
         const R T = k.T0 + th;
@@ -118,7 +135,7 @@ k_residual(const __grid_constant__ KConst<R> k, const S* __restrict__ src, doubl
     }
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        const double s = block_sum(double(v[m]), sh);
+        const double s = block_sum_r(v[m], sh);
         if (threadIdx.x == 0) partial[4 * blockIdx.x + m] = s;
     }
 }
