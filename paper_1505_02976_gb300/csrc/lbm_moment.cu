@@ -32,6 +32,7 @@ constexpr int kMBand = kMBlock - 2;    // output columns of a band, at most
 // fourth slot would save that barrier but costs two resident blocks per SM,
 // which measured slower.)
 constexpr int kMRing = 3;
+constexpr int kMaxDevices = 64;
 template <class R> struct MomentOccupancy { static constexpr int blocks = 8; };
 template <> struct MomentOccupancy<double> { static constexpr int blocks = 2; };
 
@@ -302,11 +303,15 @@ size_t moment_smem_bytes() {
 // The ring exceeds the default 48 KB of dynamic shared memory in FP64.
 template <class R, bool E, bool S>
 cudaError_t allow_smem() {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_step_m<R, E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)moment_smem_bytes<R>());
-    done = e == cudaSuccess;
+    // once per device (the attribute belongs to the function on the current device)
+    static bool done[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < kMaxDevices && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_step_m<R, E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)moment_smem_bytes<R>());
+    if (e == cudaSuccess && dev < kMaxDevices) done[dev] = true;
     return e;
 }
 
