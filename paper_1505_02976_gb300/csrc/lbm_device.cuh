@@ -680,10 +680,11 @@ __device__ __forceinline__ FastState<R> fast_moments(const KConst<R>& k, const R
 // under c_i -> -c_i so that each pair of opposite directions shares one
 // evaluation.  TAU1: tau_f = tau_T = 1, where the first term vanishes and
 // f, h are not read.  SOURCES = false drops the force and heat-source terms
-// (F_i, P_i, Q_i) and keeps the equilibria alone.
+// (F_i, P_i, Q_i) and keeps the equilibria alone.  wscale (TAU1 only)
+// multiplies every output: the FP16 storage scale folded into the weights.
 template <class R, bool TAU1, bool SOURCES = true>
 __device__ __forceinline__ void fast_collide(const KConst<R>& k, const FastState<R>& s, const R* f,
-                                             const R* h, R* fo, R* ho) {
+                                             const R* h, R* fo, R* ho, R wscale = R(1)) {
     const R uF = SOURCES ? s.uF : R(0);
     const R Fx = SOURCES ? s.Fx : R(0), Fy = SOURCES ? s.Fy : R(0);
     const R kQ = SOURCES ? k.h_kQ : R(0), uQ = SOURCES ? k.h_uQ : R(0), k0Q = SOURCES ? k.h0_kQ : R(0);
@@ -711,20 +712,22 @@ __device__ __forceinline__ void fast_collide(const KConst<R>& k, const FastState
             ho[j] = k.omT * h[j] + w * (evH - odH);
         }
     };
-    const R w1 = R(1) / R(9), w5 = R(1) / R(36);
+    const R w1 = wscale * (R(1) / R(9)), w5 = wscale * (R(1) / R(36));
     pair(1, 3, w1, ux, Fx, s.Sxx, gx, Wx);
     pair(2, 4, w1, uy, Fy, s.Syy, gy, Wy);
     pair(5, 7, w5, ux + uy, Fx + Fy, s.Sxx + s.Syy + R(2) * s.Sxy, gx + gy, Wx + Wy);
     pair(6, 8, w5, uy - ux, Fy - Fx, s.Sxx + s.Syy - R(2) * s.Sxy, gy - gx, Wy - Wx);
     const R c0 = k.h0_sig * s.th - k.h0_uu * T * uu - k.h0_pT * T * ep + k0Q;
-    ho[0] = TAU1 ? c0 : k.omT * h[0] + c0;
+    ho[0] = TAU1 ? wscale * c0 : k.omT * h[0] + c0;
 }
 
 // Interior node of one step, fast path.  Same arithmetic as node_moments +
 // eq_terms + BGK collision, rearranged for the GPU: the nine pull sources are
 // 32-bit offsets from the node (periodic wrap by per-thread deltas), plane
 // strides are uniform across the launch; then fast_moments and fast_collide.
-template <class R, class S>
+// TAU1: tau_f = tau_T = 1 (no (1 - 1/tau) terms; FP16 storage then takes its
+// scale in the collision weights).
+template <class R, class S, bool TAU1 = false>
 __device__ __forceinline__ void interior_update(const KConst<R>& k, const S* __restrict__ src,
                                                 S* __restrict__ dst, int x, int y, uint32_t step) {
     const int dxm = x == 0 ? k.nx - 1 : -1;
@@ -743,9 +746,11 @@ __device__ __forceinline__ void interior_update(const KConst<R>& k, const S* __r
     for (int i = 0; i < 9; ++i) h[i] = load_pop<S, R>(c + ((8 + i) * pl + o[i]), sc);
     const FastState<R> s = fast_moments(k, f, h, y);
     R fo[9], ho[9];
-    fast_collide<R, false>(k, s, f, h, fo, ho);
+    constexpr bool prescale = TAU1 && std::is_same<S, __half>::value;
+    if constexpr (TAU1) fast_collide<R, true>(k, s, f, h, fo, ho, prescale ? R(k.inv_scale) : R(1));
+    else fast_collide<R, false>(k, s, f, h, fo, ho);
     Dither dither((uint32_t)at, step);
-    store_planes<S, R>(dst + at, pl, fo, ho, k.inv_scale, &dither);
+    store_planes<S, R>(dst + at, pl, fo, ho, prescale ? 1.0f : k.inv_scale, &dither);
 }
 
 }  // namespace lbm

@@ -118,20 +118,22 @@ k_residual(const __grid_constant__ KConst<R> k, const S* __restrict__ src, doubl
            double* __restrict__ partial) {
     __shared__ double sh[kResBlock / 32];
     const long long N = (long long)k.nx * k.ny;
+    // the snapshot holds values of type R (FP64 conversions are slow here)
+    R* sn = reinterpret_cast<R*>(snap);
     R v[4] = {R(0), R(0), R(0), R(0)};
     for (long long c = (long long)blockIdx.x * kResBlock + threadIdx.x; c < N; c += (long long)gridDim.x * kResBlock) {
         const int y = (int)((unsigned long long)c / (unsigned)k.nx), x = (int)(c - (long long)y * k.nx);
         R ux, uy, th;
         node_u_th(k, src, x, y, &ux, &uy, &th);
         const R T = k.T0 + th;
-        const R dx = ux - R(snap[c]), dy = uy - R(snap[N + c]), dT = T - R(snap[2 * N + c]);
+        const R dx = ux - sn[c], dy = uy - sn[N + c], dT = T - sn[2 * N + c];
         v[0] += sqrt(dx * dx + dy * dy);
         v[1] += sqrt(ux * ux + uy * uy);
         v[2] += fabs(dT);
         v[3] += fabs(T);
-        snap[c] = double(ux);
-        snap[N + c] = double(uy);
-        snap[2 * N + c] = double(T);
+        sn[c] = ux;
+        sn[N + c] = uy;
+        sn[2 * N + c] = T;
     }
 #pragma unroll
     for (int m = 0; m < 4; ++m) {

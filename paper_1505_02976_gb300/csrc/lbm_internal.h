@@ -42,7 +42,8 @@ cudaError_t launch_nusselt(const KConst<R>& k, const DiagConst& d, const S* src,
                            double* nu_local, double* out, cudaStream_t st);
 
 // Residual sums (|du|, |u|, |dT|, |T|) into out[0..3] against snap (3 planes
-// of nx*ny doubles: ux, uy, T), which is overwritten with the current fields.
+// of nx*ny values of the compute type R: ux, uy, T, in a region sized for
+// doubles), which is overwritten with the current fields.
 // partial must hold 4 doubles per block of the launch (see residual_blocks).
 template <class R, class S>
 cudaError_t launch_residual(const KConst<R>& k, const S* src, double* snap, double* partial,

@@ -14,8 +14,9 @@ namespace lbm {
 
 
 // The fused step: one thread per node; interior nodes take the fast path,
-// wall nodes the NEES path.
-template <class R, class S, bool EPS_FIELD>
+// wall nodes the NEES path.  TAU1: tau_f = tau_T = 1 (the paper's default,
+// Sec. 4), where the (1 - 1/tau) terms vanish.
+template <class R, class S, bool EPS_FIELD, bool TAU1>
 __global__ void __launch_bounds__(kStepBlock, StepOccupancy<R>::blocks)
 k_step(const __grid_constant__ KConst<R> k, const S* __restrict__ src, S* __restrict__ dst, uint32_t step) {
     // Programmatic dependent launch: let the next step's blocks be scheduled
@@ -34,9 +35,9 @@ k_step(const __grid_constant__ KConst<R> k, const S* __restrict__ src, S* __rest
     if constexpr (EPS_FIELD) {
         KConst<R> kc = k;
         apply_eps(kc, node_eps(k, x, y));
-        interior_update(kc, src, dst, x, y, step);
+        interior_update<R, S, TAU1>(kc, src, dst, x, y, step);
     } else {
-        interior_update(k, src, dst, x, y, step);
+        interior_update<R, S, TAU1>(k, src, dst, x, y, step);
     }
 }
 
@@ -75,8 +76,12 @@ cudaError_t launch_step(const KConst<R>& k, const S* src, S* dst, uint32_t step,
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (k.eps_field) return cudaLaunchKernelEx(&cfg, k_step<R, S, true>, k, src, dst, step);
-    return cudaLaunchKernelEx(&cfg, k_step<R, S, false>, k, src, dst, step);
+    const bool tau1 = k.omf == R(0) && k.omT == R(0);
+    if (k.eps_field)
+        return tau1 ? cudaLaunchKernelEx(&cfg, k_step<R, S, true, true>, k, src, dst, step)
+                    : cudaLaunchKernelEx(&cfg, k_step<R, S, true, false>, k, src, dst, step);
+    return tau1 ? cudaLaunchKernelEx(&cfg, k_step<R, S, false, true>, k, src, dst, step)
+                : cudaLaunchKernelEx(&cfg, k_step<R, S, false, false>, k, src, dst, step);
 }
 
 template <class R, class S>
