@@ -7,13 +7,13 @@
 
 namespace lbm {
 
-// Residual and totals: a fixed grid of at most kResGrid blocks strides over
-// the nodes in a fixed order (deterministic).  FP64 arithmetic is slow on
-// this GPU, so the per-node work and the warp sums of the residual run in
-// the lattice's arithmetic and only the per-warp results are added in FP64;
-// the grid is large enough that every node's loads are in flight at once.
+// Residual and totals: a grid of at most kResGrid blocks strides over the
+// nodes in a fixed order (deterministic; one node per thread up to 16.7 M
+// nodes).  FP64 arithmetic is slow on this GPU, so the per-node work and the
+// warp sums of the residual run in the lattice's arithmetic and only the
+// per-warp results are added in FP64.
 constexpr int kResBlock = 256;
-constexpr int kResGrid = 8192;
+constexpr int kResGrid = 65536;
 
 // Block sum of one value per thread: warp sums in R, then the warps' sums
 // in FP64 in a fixed order (valid in thread 0).
@@ -123,10 +123,12 @@ k_residual(const __grid_constant__ KConst<R> k, const S* __restrict__ src, doubl
     R v[4] = {R(0), R(0), R(0), R(0)};
     for (long long c = (long long)blockIdx.x * kResBlock + threadIdx.x; c < N; c += (long long)gridDim.x * kResBlock) {
         const int y = (int)((unsigned long long)c / (unsigned)k.nx), x = (int)(c - (long long)y * k.nx);
+        // snapshot loads first: they do not depend on the node's moments
+        const R s0 = sn[c], s1 = sn[N + c], s2 = sn[2 * N + c];
         R ux, uy, th;
         node_u_th(k, src, x, y, &ux, &uy, &th);
         const R T = k.T0 + th;
-        const R dx = ux - sn[c], dy = uy - sn[N + c], dT = T - sn[2 * N + c];
+        const R dx = ux - s0, dy = uy - s1, dT = T - s2;
         v[0] += sqrt(dx * dx + dy * dy);
         v[1] += sqrt(ux * ux + uy * uy);
         v[2] += fabs(dT);
@@ -169,10 +171,13 @@ k_totals(const __grid_constant__ KConst<R> k, const S* __restrict__ src, double 
     }
 }
 
-__global__ void k_reduce4(const double* __restrict__ partial, long long nb, double* __restrict__ out) {
-    __shared__ double sh[kReduceBlock / 32];
+constexpr int kReduce4Block = 1024;
+
+__global__ void __launch_bounds__(kReduce4Block) k_reduce4(const double* __restrict__ partial, long long nb,
+                                                          double* __restrict__ out) {
+    __shared__ double sh[kReduce4Block / 32];
     double a[4] = {0.0, 0.0, 0.0, 0.0};
-    for (long long b = threadIdx.x; b < nb; b += kReduceBlock)
+    for (long long b = threadIdx.x; b < nb; b += kReduce4Block)
 #pragma unroll
         for (int m = 0; m < 4; ++m) a[m] += partial[4 * b + m];
 #pragma unroll
@@ -293,7 +298,7 @@ cudaError_t launch_residual(const KConst<R>& k, const S* src, double* snap, doub
     k_residual<R, S><<<(unsigned)residual_blocks(k.nx, k.ny), kResBlock, 0, st>>>(k, src, snap, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_reduce4<<<1, kReduceBlock, 0, st>>>(partial, residual_blocks(k.nx, k.ny), out);
+    k_reduce4<<<1, kReduce4Block, 0, st>>>(partial, residual_blocks(k.nx, k.ny), out);
     return cudaGetLastError();
 }
 
@@ -303,7 +308,7 @@ cudaError_t launch_totals(const KConst<R>& k, const S* src, double sT0, double* 
     k_totals<R, S><<<(unsigned)residual_blocks(k.nx, k.ny), kResBlock, 0, st>>>(k, src, sT0, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_reduce4<<<1, kReduceBlock, 0, st>>>(partial, residual_blocks(k.nx, k.ny), out);
+    k_reduce4<<<1, kReduce4Block, 0, st>>>(partial, residual_blocks(k.nx, k.ny), out);
     return cudaGetLastError();
 }
 
