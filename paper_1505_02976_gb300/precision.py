@@ -38,4 +38,8 @@ def run(problem: dict, precision: str, steps: int, device: int = 0):
 
 def compare(problem: dict, steps: int, precisions=("f32", "f16"), device: int = 0) -> dict:
     ref, nu_ref = run(problem, "f64", steps, device)
-    return {p: field_errors(*run(problem, p, steps, device), ref, nu_ref) for p in precisions}
+    out = {}
+    for p in precisions:
+        m, nu = run(problem, p, steps, device)
+        out[p] = field_errors(m, ref, nu, nu_ref)
+    return out
