@@ -40,7 +40,7 @@ BYTES_PER_CELL = {"f64": 17 * 8 * 2, "f32": 17 * 4 * 2, "f16": 17 * 2 * 2,
 METRIC = "coupled flow+thermal MLUPS and % HBM roofline at 1 GB300 (plain FP32 fused step)"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_f32_2048_traffic.json")
 KERNEL_SOURCES = ("paper_1505_02976_gb300/csrc/lbm_device.cuh", "paper_1505_02976_gb300/csrc/lbm_step.cuh",
-                  "paper_1505_02976_gb300/csrc/lbm_kernels.cu")
+                  "paper_1505_02976_gb300/csrc/lbm_kernels.cu", "paper_1505_02976_gb300/csrc/lbm_step_tma.cu")
 
 
 def kernel_source_hash() -> str:

@@ -172,11 +172,19 @@ lbm_status lbm_create(const lbm_params* p, void* stream, void* workspace, size_t
     h->cur = 0;
     h->steps = h->launches = 0;
     h->nonfinite = false;
+    h->timeout = false;
     h->mcur = 0;
     h->msources = false;
     h->pops_valid = false;
     h->k64 = make_kconst<double>(p, d, L, h->flag());
     h->k32 = make_kconst<float>(p, d, L, h->flag());
+    h->tma = false;
+    h->tma_rows = 0;
+    if (p->precision == LBM_F32 && !p->moment_state && lbm::tma_step_supported(h->k32)) {
+        h->tma = lbm::make_step_tensor_map(h->k32, (const float*)h->buf(0), &h->tmap[0]) &&
+                 lbm::make_step_tensor_map(h->k32, (const float*)h->buf(1), &h->tmap[1]);
+        h->tma_rows = lbm::tma_rows_default(h->k32);
+    }
     h->msegments = 1;
     if (p->moment_state)
         h->msegments = p->precision == LBM_F64 ? lbm::moment_segments_default(h->k64)
@@ -263,11 +271,13 @@ lbm_status lbm_set_fields(lbm_handle* h, const double* T, const double* ux, cons
     if (!on_device) LBM_CUDA(h, cudaStreamSynchronize(h->stream), "set_fields");
     h->steps = 0;
     h->nonfinite = false;
+    h->timeout = false;
     return LBM_OK;
 }
 
 lbm_status lbm_step(lbm_handle* h, int64_t n) {
     if (!h || n < 0) return h ? fail(h, LBM_ERR_ARG, "negative step count") : LBM_ERR_ARG;
+    if (h->timeout) return fail(h, LBM_ERR_TIMEOUT, "a bounded wait of the TMA step gave up");
     if (h->nonfinite) return fail(h, LBM_ERR_NONFINITE, "non-finite velocity or temperature");
     if (h->moments_kind()) {
         for (int64_t i = 0; i < n; ++i) {
@@ -288,6 +298,15 @@ lbm_status lbm_step(lbm_handle* h, int64_t n) {
     }
     for (int64_t i = 0; i < n; ++i) {
         const int src = h->cur, dst = 1 - h->cur;
+        if (h->tma) {
+            cudaError_t e = lbm::launch_step_tma(h->k32, h->tmap[src], (const float*)h->buf(src), (float*)h->buf(dst),
+                                                 h->tma_rows, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "step kernel (TMA)");
+            h->cur = dst;
+            ++h->steps;
+            ++h->launches;
+            continue;
+        }
         cudaError_t e = dispatch(h, [&](auto& k, auto* tag) {
             using S = std::remove_pointer_t<decltype(tag)>;
             return lbm::launch_step(k, (const S*)h->buf(src), (S*)h->buf(dst), (uint32_t)h->steps, h->stream);
@@ -315,7 +334,9 @@ lbm_status lbm_sync(lbm_handle* h) {
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "stream synchronise");
     int flag = 0;
     LBM_CUDA(h, cudaMemcpy(&flag, h->flag(), sizeof(int), cudaMemcpyDeviceToHost), "flag read");
-    if (flag) h->nonfinite = true;
+    if (flag & 2) h->timeout = true;
+    if (flag & 1) h->nonfinite = true;
+    if (h->timeout) return fail(h, LBM_ERR_TIMEOUT, "a bounded wait of the TMA step gave up");
     if (h->nonfinite) return fail(h, LBM_ERR_NONFINITE, "non-finite velocity or temperature");
     return LBM_OK;
 }
@@ -448,6 +469,7 @@ lbm_status lbm_set_state(lbm_handle* h, const double* f, const double* g, int on
         LBM_CUDA(h, cudaStreamSynchronize(h->stream), "set_state");
     }
     h->nonfinite = false;
+    h->timeout = false;
     return LBM_OK;
 }
 
@@ -617,6 +639,7 @@ lbm_status lbm_checkpoint(lbm_handle* h, const char* path, int save) {
     LBM_CUDA(h, cudaMemset(h->flag(), 0, sizeof(int)), "flag reset");
     h->steps = hd.steps;
     h->nonfinite = false;
+    h->timeout = false;
     return LBM_OK;
 }
 

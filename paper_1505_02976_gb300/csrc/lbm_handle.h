@@ -23,7 +23,12 @@ struct lbm_handle {
     int mcur;
     bool msources, pops_valid;
     int msegments;  // row segments per band of the moment step
-    bool nonfinite;
+    // FP32 walled lattices: the step with TMA-staged rows (tensor maps of the
+    // two population buffers) and its rows per block segment
+    bool tma;
+    CUtensorMap tmap[2];
+    int tma_rows;
+    bool nonfinite, timeout;
     lbm::KConst<double> k64;
     lbm::KConst<float> k32;
     lbm::DiagConst diag;

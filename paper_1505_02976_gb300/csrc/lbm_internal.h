@@ -1,6 +1,7 @@
 // lbm_internal.h -- launch wrappers shared by the host API and the kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
@@ -117,6 +118,16 @@ cudaError_t launch_init_m(const KConst<R>& k, R* dst, const double* T, const dou
 // Row segments per band that fill the GPU's resident blocks once.
 template <class R>
 int moment_segments_default(const KConst<R>& k);
+
+// ------------------------------------------- FP32 step with TMA-staged rows
+// Lattices walled on all four sides, FP32 storage: the tensor map of a
+// population buffer (false if the driver's encoder is unavailable or
+// rejects it), the default rows per block segment, and the launch.
+bool tma_step_supported(const KConst<float>& k);
+bool make_step_tensor_map(const KConst<float>& k, const float* buf, CUtensorMap* out);
+int tma_rows_default(const KConst<float>& k);
+cudaError_t launch_step_tma(const KConst<float>& k, const CUtensorMap& tm, const float* src, float* dst, int rows,
+                            cudaStream_t st);
 
 // Resident blocks per SM of the batched step kernel.
 template <class R, class S>

@@ -1,0 +1,248 @@
+// lbm_step_tma.cu -- the FP32 step with its loads staged by the tensor
+// memory accelerator (TMA).
+//
+// Same per-node arithmetic as k_step (fast_moments and fast_collide for
+// interior nodes, the out-of-line NEES path for wall nodes), but the 17
+// pulled values of every interior node reach the block through shared
+// memory.  Pull streaming reads plane i of output row y from global row
+// y - c_iy, so each plane of each global row is used by exactly one output
+// row: a slot holds the 17 planes one output row needs, each plane
+// loaded (one 3-D tensor copy, 136 columns x 1 row x 1 plane) from its own
+// source row.  A block owns a band of 128 columns and a segment of up to
+// kTRows rows; one thread issues all of the block's copies (17 plane rows
+// per output row, 37 KB for 4 rows) at its start, and the threads wait on
+// each row's mbarrier instead of on their own global loads.  Many short
+// blocks keep the SMs busy to the end of the step (measured on the 2048^2
+// and 8192^2 FP32 cavities: 4-row segments beat 2, 3, 5, 6, 8, 16, 32 and
+// 64 rows streamed through a ring of 2 to 6 row slots, and the global-load
+// step).
+//
+// Wall nodes (the segment's part of the W and E columns, and the S and N
+// rows) are updated before the row loop, all in parallel, while the first
+// rows' loads are in flight; the row loop then runs interior nodes only.
+//
+// Used for FP32 storage on lattices walled on all four sides (a periodic
+// side would need wrapped halo columns, which the tile load does not give):
+// every interior node pulls only from nodes inside the lattice, and the
+// zero fill of out-of-range boxes is never read.  Waits are bounded: a wait
+// that gives up sets bit 1 of the handle's flag (LBM_ERR_TIMEOUT) and the
+// block stops after its copies in flight have landed.
+#include <cuda.h>
+#include <math.h>
+
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+constexpr int kTBand = 128;                 // output columns per band = threads per block
+constexpr int kTHalo = 4;                   // columns loaded left of the band (16-byte aligned x)
+constexpr int kTBox = kTBand + 2 * kTHalo;  // 136 columns per loaded plane row
+// A tensor copy's shared-memory destination must be 128-byte aligned: each
+// plane row of a slot is padded to 160 floats (640 bytes).
+constexpr int kTPlane = 160;
+constexpr int kTSlot = NPLANES * kTPlane;  // floats per slot (one output row)
+constexpr unsigned kTBytes = (unsigned)(NPLANES * kTBox) * sizeof(float);  // bytes landing per slot
+static_assert(kTPlane >= kTBox && kTPlane * sizeof(float) % 128 == 0, "plane rows must stay 128-byte aligned");
+#ifndef LBM_TMA_ROWS
+#define LBM_TMA_ROWS 4
+#endif
+constexpr int kTRows = LBM_TMA_ROWS;  // output rows staged per block (the segment's interior rows)
+constexpr long long kTWaitLimit = 1ll << 26;  // try_wait polls before a wait gives up
+
+// slots, barriers, and room to round the first slot up to 128 bytes
+constexpr size_t kTSmem = 128 + (size_t)kTRows * kTSlot * sizeof(float) + kTRows * sizeof(uint64_t);
+// resident blocks per SM that the shared memory allows (228 KB per SM, 1 KB
+// reserved per block), at most 8
+constexpr int kTBlocks = (int)((228 * 1024) / (kTSmem + 1024)) < 8 ? (int)((228 * 1024) / (kTSmem + 1024)) : 8;
+
+// Source row offset (-c_iy) and column offset (-c_ix) of each stored plane:
+// planes 0..7 hold f_1..f_8, planes 8..16 h_0..h_8; c: 1 (+1,0) 2 (0,+1)
+// 3 (-1,0) 4 (0,-1) 5 (+1,+1) 6 (-1,+1) 7 (-1,-1) 8 (+1,-1).
+__host__ __device__ constexpr int plane_dy(int p) {
+    constexpr int d[NPLANES] = {0, -1, 0, 1, -1, -1, 1, 1, 0, 0, -1, 0, 1, -1, -1, 1, 1};
+    return d[p];
+}
+__host__ __device__ constexpr int plane_dx(int p) {
+    constexpr int d[NPLANES] = {-1, 0, 1, 0, -1, 1, 1, -1, 0, -1, 0, 1, 0, -1, 1, 1, -1};
+    return d[p];
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// The 17 plane rows output row y pulls from, into one slot: plane p from
+// global row y + plane_dy(p), columns x0 - 4 .. x0 + 131.
+__device__ __forceinline__ void tma_load_slot(const CUtensorMap* tm, float* slot, uint64_t* bar, int x, int y) {
+    const uint32_t b = smem_addr(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(kTBytes) : "memory");
+#pragma unroll
+    for (int p = 0; p < NPLANES; ++p)
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4}], [%5];" ::"r"(smem_addr(slot + p * kTPlane)),
+            "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y + plane_dy(p)), "r"(p), "r"(b)
+            : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false if it gave up.
+__device__ __forceinline__ bool tma_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t b = smem_addr(bar);
+    for (long long i = 0; i < kTWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <bool EPS_FIELD, bool TAU1>
+__global__ void __launch_bounds__(kTBand, kTBlocks)
+k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUtensorMap tm,
+           const float* __restrict__ src, float* __restrict__ dst, int rows) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    float* stage = reinterpret_cast<float*>(base);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)kTRows * kTSlot * sizeof(float));
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kTBand;
+    const int y0 = blockIdx.y * rows;
+    const int y1 = min(y0 + rows, k.ny);
+    const int yb = max(y0, 1), ye = min(y1, k.ny - 1);  // interior rows of the segment (at most kTRows)
+    const int x = x0 + tid;
+    if (tid == 0) {
+        for (int s = 0; s < kTRows; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar + s)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // the previous step's writes must be visible before the first load
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // output row r lands in slot r - yb (each slot and barrier is used once)
+    if (tid == 0)
+        for (int r = yb; r < ye; ++r) tma_load_slot(&tm, stage + (r - yb) * kTSlot, bar + (r - yb), x0 - kTHalo, r);
+    // wall nodes of the segment, in parallel, while those loads fly
+    if (x < k.nx) {
+        if (y0 == 0) wall_update(k, src, dst, x, 0, 0u);
+        if (y1 == k.ny) wall_update(k, src, dst, x, k.ny - 1, 0u);
+    }
+    if (x0 == 0)
+        for (int y = yb + tid; y < ye; y += kTBand) wall_update(k, src, dst, 0, y, 0u);
+    if (x0 <= k.nx - 1 && k.nx - 1 < x0 + kTBand)
+        for (int y = yb + tid; y < ye; y += kTBand) wall_update(k, src, dst, k.nx - 1, y, 0u);
+    const bool active = x >= 1 && x <= k.nx - 2;
+    const int c = tid + kTHalo;
+    // every decision to go on is taken by the whole block (__syncthreads_and),
+    // so no thread can leave the loop while others wait at a barrier
+    bool ok = true;
+    for (int y = yb; y < ye; ++y) {
+        ok = __syncthreads_and(tma_wait(bar + (y - yb), 0u));
+        if (!ok) break;
+        if (active) {
+            const float* sl = stage + (y - yb) * kTSlot + c;
+            float f[9], h[9];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) f[i] = sl[(i - 1) * kTPlane + plane_dx(i - 1)];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) h[i] = sl[(8 + i) * kTPlane + plane_dx(8 + i)];
+            float fo[9], ho[9];
+            if constexpr (EPS_FIELD) {
+                KConst<float> kc = k;
+                apply_eps(kc, node_eps(k, x, y));
+                fast_collide<float, TAU1>(kc, fast_moments(kc, f, h, y), f, h, fo, ho);
+            } else {
+                fast_collide<float, TAU1>(k, fast_moments(k, f, h, y), f, h, fo, ho);
+            }
+            store_planes<float, float>(dst + (y * k.pitch + x), k.plane32, fo, ho, 1.0f, nullptr);
+        }
+    }
+    if (!ok && tid == 0) {
+        atomicOr(k.flag, 2);
+        // let this block's copies land before its shared memory is released
+        for (int r = yb; r < ye; ++r) (void)tma_wait(bar + (r - yb), 0u);
+    }
+}
+
+// The tensor map of one population buffer: dims (x: nx, y: ny, plane: 17),
+// box (136, 1, 1), zero fill outside.
+bool make_step_tensor_map(const KConst<float>& k, const float* buf, CUtensorMap* out) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<Encode>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)k.nx, (cuuint64_t)k.ny, (cuuint64_t)NPLANES};
+    const cuuint64_t strides[2] = {(cuuint64_t)k.pitch * sizeof(float), (cuuint64_t)k.plane * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)kTBox, 1u, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(buf), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool tma_step_supported(const KConst<float>& k) {
+    for (int s = 0; s < 4; ++s)
+        if (k.bc[s] == BC_PERIODIC) return false;
+    return k.nx >= 4 && k.ny >= 4;
+}
+
+int tma_rows_default(const KConst<float>&) { return kTRows; }
+
+// Slots beyond the default 48 KB of dynamic shared memory need the
+// function's opt-in, once per device.
+template <bool E, bool T>
+static cudaError_t allow_tma_smem() {
+    if (kTSmem <= 48 * 1024) return cudaSuccess;
+    constexpr int kMaxDev = 64;
+    static bool done[kMaxDev] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < kMaxDev && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_step_tma<E, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
+    if (e == cudaSuccess && dev < kMaxDev) done[dev] = true;
+    return e;
+}
+
+template <bool E, bool T>
+static cudaError_t launch_tma(const cudaLaunchConfig_t& cfg, const KConst<float>& k, const CUtensorMap& tm,
+                              const float* src, float* dst, int rows) {
+    cudaError_t e = allow_tma_smem<E, T>();
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, k_step_tma<E, T>, k, tm, src, dst, rows);
+}
+
+cudaError_t launch_step_tma(const KConst<float>& k, const CUtensorMap& tm, const float* src, float* dst, int rows,
+                            cudaStream_t st) {
+    if (rows < 1 || rows > kTRows) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((k.nx + kTBand - 1) / kTBand), (unsigned)((k.ny + rows - 1) / rows));
+    cfg.blockDim = dim3(kTBand);
+    cfg.dynamicSmemBytes = kTSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const bool tau1 = k.omf == 0.f && k.omT == 0.f;
+    if (k.eps_field)
+        return tau1 ? launch_tma<true, true>(cfg, k, tm, src, dst, rows) : launch_tma<true, false>(cfg, k, tm, src, dst, rows);
+    return tau1 ? launch_tma<false, true>(cfg, k, tm, src, dst, rows) : launch_tma<false, false>(cfg, k, tm, src, dst, rows);
+}
+
+}  // namespace lbm
