@@ -33,7 +33,8 @@
  *   the workspace (caller-provided or allocated by lbm_create).
  * Errors: every entry point returns an lbm_status; no exception or abort
  *   crosses the ABI.  lbm_last_error() gives a message for the last failure.
- *   LBM_ERR_NONFINITE is sticky until lbm_set_fields or lbm_set_state.
+ *   LBM_ERR_NONFINITE and LBM_ERR_TIMEOUT are sticky until lbm_set_fields
+ *   or lbm_set_state.
  * Threading: a handle must not be used from two threads at once.
  */
 #ifndef LBM_GB300_H
@@ -123,6 +124,20 @@ typedef struct {
  * handle. */
 lbm_status lbm_set_moment_segments(lbm_handle* h, int32_t segments);
 
+/* Step kernel of a population handle (no counterpart in the paper; a
+ * launch choice).  FP32 and FP16 lattices walled on all four sides default
+ * to staged rows: each block loads the 17 planes its rows pull from into
+ * shared memory with tensor copies and waits on them with bounded waits.
+ * staged = 0 selects the kernel in which every thread loads its own 17
+ * values from global memory; staged = 1 restores the staged kernel
+ * (LBM_ERR_ARG where it is unavailable: FP64, a periodic side, the moment
+ * state, a lattice under 4 x 4, or a driver without tensor-map encoding).
+ * Both kernels run the same per-node arithmetic (results agree to rounding;
+ * bit for bit at tau_f = tau_T = 1).  lbm_step_staged returns 1 when the
+ * next step uses staged rows, else 0. */
+lbm_status lbm_set_step_staging(lbm_handle* h, int32_t staged);
+int32_t lbm_step_staged(const lbm_handle* h);
+
 /* Fill p with the paper's defaults (Sec. 4): the 32 x 32 porous cavity,
  * hot W wall T = 1, cold E wall T = 0, adiabatic S and N, no slip, rho0 = 1,
  * J = sigma = 1, tau_f = tau_T = 1, Ma = 0.1, Ra = 1e3, Da = 1e-2,
@@ -188,12 +203,24 @@ lbm_status lbm_set_force_profile(lbm_handle* h, const double* ay);
 
 /* Advance n >= 0 time steps (stream, rebuild walls, collide; one kernel
  * launch per step).  Asynchronous on the handle's stream.  Returns
- * LBM_ERR_NONFINITE if an earlier synchronising call saw the flag. */
+ * LBM_ERR_NONFINITE or LBM_ERR_TIMEOUT if an earlier synchronising call saw
+ * the corresponding flag.  FP32 lattices walled on all four sides stage the
+ * pulled rows in shared memory with tensor copies and bounded waits. */
 lbm_status lbm_step(lbm_handle* h, int64_t n);
 
-/* Wait for the handle's stream; returns LBM_ERR_NONFINITE if any step since
- * the last reset produced a non-finite velocity or temperature. */
+/* Wait for the handle's stream; returns LBM_ERR_TIMEOUT if a bounded
+ * device-side wait of a step gave up (the state is then undefined), else
+ * LBM_ERR_NONFINITE if any step since the last reset produced a non-finite
+ * velocity or temperature. */
 lbm_status lbm_sync(lbm_handle* h);
+
+/* Failure-detection self-test (the paper has no counterpart): launches, on
+ * the handle's stream, one kernel whose bounded device-side wait cannot
+ * succeed (an mbarrier that nothing arrives on, 20 ms limit); it gives up
+ * and raises the handle's timeout flag, so the next lbm_sync returns
+ * LBM_ERR_TIMEOUT and the context stays usable.  lbm_set_fields or
+ * lbm_set_state clear the status.  Asynchronous. */
+lbm_status lbm_wait_selftest(lbm_handle* h);
 
 /* Macroscopic fields of the current state: the pressure, velocity and
  * temperature that the next step computes after streaming (Sec. 3.1-3.2);

@@ -178,11 +178,16 @@ lbm_status lbm_create(const lbm_params* p, void* stream, void* workspace, size_t
     h->pops_valid = false;
     h->k64 = make_kconst<double>(p, d, L, h->flag());
     h->k32 = make_kconst<float>(p, d, L, h->flag());
-    h->tma = false;
+    h->tma = h->tma_ready = false;
     h->tma_rows = 0;
-    if (p->precision == LBM_F32 && !p->moment_state && lbm::tma_step_supported(h->k32)) {
-        h->tma = lbm::make_step_tensor_map(h->k32, (const float*)h->buf(0), &h->tmap[0]) &&
-                 lbm::make_step_tensor_map(h->k32, (const float*)h->buf(1), &h->tmap[1]);
+    if (p->precision != LBM_F64 && !p->moment_state && lbm::tma_step_supported(h->k32)) {
+        if (p->precision == LBM_F32)
+            h->tma_ready = lbm::make_step_tensor_map(h->k32, (const float*)h->buf(0), &h->tmap[0]) &&
+                           lbm::make_step_tensor_map(h->k32, (const float*)h->buf(1), &h->tmap[1]);
+        else
+            h->tma_ready = lbm::make_step_tensor_map(h->k32, (const __half*)h->buf(0), &h->tmap[0]) &&
+                           lbm::make_step_tensor_map(h->k32, (const __half*)h->buf(1), &h->tmap[1]);
+        h->tma = h->tma_ready;
         h->tma_rows = lbm::tma_rows_default(h->k32);
     }
     h->msegments = 1;
@@ -299,8 +304,12 @@ lbm_status lbm_step(lbm_handle* h, int64_t n) {
     for (int64_t i = 0; i < n; ++i) {
         const int src = h->cur, dst = 1 - h->cur;
         if (h->tma) {
-            cudaError_t e = lbm::launch_step_tma(h->k32, h->tmap[src], (const float*)h->buf(src), (float*)h->buf(dst),
-                                                 h->tma_rows, h->stream);
+            const uint32_t step = (uint32_t)h->steps;
+            cudaError_t e = h->prm.precision == LBM_F32
+                                ? lbm::launch_step_tma(h->k32, h->tmap[src], (const float*)h->buf(src),
+                                                       (float*)h->buf(dst), h->tma_rows, step, h->stream)
+                                : lbm::launch_step_tma(h->k32, h->tmap[src], (const __half*)h->buf(src),
+                                                       (__half*)h->buf(dst), h->tma_rows, step, h->stream);
             if (e != cudaSuccess) return cuda_fail(h, e, "step kernel (TMA)");
             h->cur = dst;
             ++h->steps;
@@ -318,6 +327,16 @@ lbm_status lbm_step(lbm_handle* h, int64_t n) {
     }
     return LBM_OK;
 }
+
+lbm_status lbm_set_step_staging(lbm_handle* h, int32_t staged) {
+    if (!h) return LBM_ERR_ARG;
+    if (staged && !h->tma_ready)
+        return fail(h, LBM_ERR_ARG, "staged rows need FP32 or FP16 populations on a lattice walled on all sides");
+    h->tma = staged != 0;
+    return LBM_OK;
+}
+
+int32_t lbm_step_staged(const lbm_handle* h) { return h && h->tma ? 1 : 0; }
 
 lbm_status lbm_set_moment_segments(lbm_handle* h, int32_t segments) {
     if (!h) return LBM_ERR_ARG;
@@ -338,6 +357,14 @@ lbm_status lbm_sync(lbm_handle* h) {
     if (flag & 1) h->nonfinite = true;
     if (h->timeout) return fail(h, LBM_ERR_TIMEOUT, "a bounded wait of the TMA step gave up");
     if (h->nonfinite) return fail(h, LBM_ERR_NONFINITE, "non-finite velocity or temperature");
+    return LBM_OK;
+}
+
+lbm_status lbm_wait_selftest(lbm_handle* h) {
+    if (!h) return LBM_ERR_ARG;
+    cudaError_t e = lbm::launch_wait_selftest(h->flag(), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "wait self-test kernel");
+    ++h->launches;
     return LBM_OK;
 }
 

@@ -23,9 +23,10 @@ struct lbm_handle {
     int mcur;
     bool msources, pops_valid;
     int msegments;  // row segments per band of the moment step
-    // FP32 walled lattices: the step with TMA-staged rows (tensor maps of the
-    // two population buffers) and its rows per block segment
-    bool tma;
+    // FP32 / FP16 walled lattices: the step with TMA-staged rows (tensor maps
+    // of the two population buffers, whether they could be made, whether
+    // the step uses them) and its rows per block segment
+    bool tma, tma_ready;
     CUtensorMap tmap[2];
     int tma_rows;
     bool nonfinite, timeout;

@@ -119,15 +119,20 @@ cudaError_t launch_init_m(const KConst<R>& k, R* dst, const double* T, const dou
 template <class R>
 int moment_segments_default(const KConst<R>& k);
 
-// ------------------------------------------- FP32 step with TMA-staged rows
-// Lattices walled on all four sides, FP32 storage: the tensor map of a
-// population buffer (false if the driver's encoder is unavailable or
-// rejects it), the default rows per block segment, and the launch.
+// ------------------------------------------- step with TMA-staged rows
+// Lattices walled on all four sides, FP32 or FP16 storage (S): the tensor
+// map of a population buffer (false if the driver's encoder is unavailable
+// or rejects it), the default rows per block segment, and the launch (step
+// numbers the FP16 stochastic rounding).
 bool tma_step_supported(const KConst<float>& k);
-bool make_step_tensor_map(const KConst<float>& k, const float* buf, CUtensorMap* out);
+template <class S>
+bool make_step_tensor_map(const KConst<float>& k, const S* buf, CUtensorMap* out);
 int tma_rows_default(const KConst<float>& k);
-cudaError_t launch_step_tma(const KConst<float>& k, const CUtensorMap& tm, const float* src, float* dst, int rows,
-                            cudaStream_t st);
+template <class S>
+cudaError_t launch_step_tma(const KConst<float>& k, const CUtensorMap& tm, const S* src, S* dst, int rows,
+                            uint32_t step, cudaStream_t st);
+// One wait that must give up (nothing arrives): sets bit 1 of *flag.
+cudaError_t launch_wait_selftest(int* flag, cudaStream_t st);
 
 // Resident blocks per SM of the batched step kernel.
 template <class R, class S>

@@ -1,5 +1,5 @@
-// lbm_step_tma.cu -- the FP32 step with its loads staged by the tensor
-// memory accelerator (TMA).
+// lbm_step_tma.cu -- the FP32 / FP16-storage step with its loads staged by
+// the tensor memory accelerator (TMA).
 //
 // Same per-node arithmetic as k_step (fast_moments and fast_collide for
 // interior nodes, the out-of-line NEES path for wall nodes), but the 17
@@ -7,10 +7,10 @@
 // memory.  Pull streaming reads plane i of output row y from global row
 // y - c_iy, so each plane of each global row is used by exactly one output
 // row: a slot holds the 17 planes one output row needs, each plane
-// loaded (one 3-D tensor copy, 136 columns x 1 row x 1 plane) from its own
-// source row.  A block owns a band of 128 columns and a segment of up to
+// loaded (one 3-D tensor copy of 128 + 2 halo columns x 1 row x 1 plane)
+// from its own source row.  A block owns a band of 128 columns and a segment of up to
 // kTRows rows; one thread issues all of the block's copies (17 plane rows
-// per output row, 37 KB for 4 rows) at its start, and the threads wait on
+// per output row, 37 KB for 4 FP32 rows) at its start, and the threads wait on
 // each row's mbarrier instead of on their own global loads.  Many short
 // blocks keep the SMs busy to the end of the step (measured on the 2048^2
 // and 8192^2 FP32 cavities: 4-row segments beat 2, 3, 5, 6, 8, 16, 32 and
@@ -21,7 +21,7 @@
 // rows) are updated before the row loop, all in parallel, while the first
 // rows' loads are in flight; the row loop then runs interior nodes only.
 //
-// Used for FP32 storage on lattices walled on all four sides (a periodic
+// Used for FP32 and FP16 storage on lattices walled on all four sides (a periodic
 // side would need wrapped halo columns, which the tile load does not give):
 // every interior node pulls only from nodes inside the lattice, and the
 // zero fill of out-of-range boxes is never read.  Waits are bounded: a wait
@@ -30,30 +30,39 @@
 #include <cuda.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "lbm_step.cuh"
 
 namespace lbm {
 
-constexpr int kTBand = 128;                 // output columns per band = threads per block
-constexpr int kTHalo = 4;                   // columns loaded left of the band (16-byte aligned x)
-constexpr int kTBox = kTBand + 2 * kTHalo;  // 136 columns per loaded plane row
-// A tensor copy's shared-memory destination must be 128-byte aligned: each
-// plane row of a slot is padded to 160 floats (640 bytes).
-constexpr int kTPlane = 160;
-constexpr int kTSlot = NPLANES * kTPlane;  // floats per slot (one output row)
-constexpr unsigned kTBytes = (unsigned)(NPLANES * kTBox) * sizeof(float);  // bytes landing per slot
-static_assert(kTPlane >= kTBox && kTPlane * sizeof(float) % 128 == 0, "plane rows must stay 128-byte aligned");
+constexpr int kTBand = 128;  // output columns per band = threads per block
 #ifndef LBM_TMA_ROWS
 #define LBM_TMA_ROWS 4
 #endif
 constexpr int kTRows = LBM_TMA_ROWS;  // output rows staged per block (the segment's interior rows)
-constexpr long long kTWaitLimit = 1ll << 26;  // try_wait polls before a wait gives up
+constexpr unsigned long long kTWaitNs = 2000000000ull;  // a wait gives up after 2 s
+constexpr long long kTWaitPolls = 1ll << 28;             // ... or after this many polls
 
-// slots, barriers, and room to round the first slot up to 128 bytes
-constexpr size_t kTSmem = 128 + (size_t)kTRows * kTSlot * sizeof(float) + kTRows * sizeof(uint64_t);
-// resident blocks per SM that the shared memory allows (228 KB per SM, 1 KB
-// reserved per block), at most 8
-constexpr int kTBlocks = (int)((228 * 1024) / (kTSmem + 1024)) < 8 ? (int)((228 * 1024) / (kTSmem + 1024)) : 8;
+// Shared-memory layout of the staged rows for storage type S.  A copy starts
+// `halo` columns left of the band so that its x coordinate stays a multiple
+// of 16 bytes; a copy's shared-memory destination must be 128-byte aligned,
+// so each plane row of a slot is padded to a multiple of 128 bytes.
+template <class S>
+struct TmaLayout {
+    static constexpr int halo = 16 / (int)sizeof(S);                        // 4 (FP32), 8 (FP16)
+    static constexpr int box = kTBand + 2 * halo;                           // 136, 144 columns
+    static constexpr int plane = ((box * (int)sizeof(S) + 127) / 128) * 128 / (int)sizeof(S);  // 160, 192
+    static constexpr int slot = NPLANES * plane;                            // elements per slot
+    static constexpr unsigned bytes = (unsigned)(NPLANES * box * sizeof(S));  // bytes landing per slot
+    // slots, barriers, and room to round the first slot up to 128 bytes
+    static constexpr size_t smem = 128 + (size_t)kTRows * slot * sizeof(S) + kTRows * sizeof(uint64_t);
+    // resident blocks per SM that the shared memory allows (228 KB per SM,
+    // 1 KB reserved per block), at most 8
+    static constexpr int blocks = (int)((228 * 1024) / (smem + 1024)) < 8 ? (int)((228 * 1024) / (smem + 1024)) : 8;
+};
+static_assert(TmaLayout<float>::plane * sizeof(float) % 128 == 0, "plane rows must stay 128-byte aligned");
+static_assert(TmaLayout<__half>::plane * sizeof(__half) % 128 == 0, "plane rows must stay 128-byte aligned");
 
 // Source row offset (-c_iy) and column offset (-c_ix) of each stored plane:
 // planes 0..7 hold f_1..f_8, planes 8..16 h_0..h_8; c: 1 (+1,0) 2 (0,+1)
@@ -72,23 +81,34 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 }
 
 // The 17 plane rows output row y pulls from, into one slot: plane p from
-// global row y + plane_dy(p), columns x0 - 4 .. x0 + 131.
-__device__ __forceinline__ void tma_load_slot(const CUtensorMap* tm, float* slot, uint64_t* bar, int x, int y) {
+// global row y + plane_dy(p), columns x0 - halo .. x0 + 127 + halo.
+template <class S>
+__device__ __forceinline__ void tma_load_slot(const CUtensorMap* tm, S* slot, uint64_t* bar, int x, int y) {
+    using L = TmaLayout<S>;
     const uint32_t b = smem_addr(bar);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(kTBytes) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(L::bytes) : "memory");
 #pragma unroll
     for (int p = 0; p < NPLANES; ++p)
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-            "%4}], [%5];" ::"r"(smem_addr(slot + p * kTPlane)),
+            "%4}], [%5];" ::"r"(smem_addr(slot + p * L::plane)),
             "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y + plane_dy(p)), "r"(p), "r"(b)
             : "memory");
 }
 
-// Bounded wait for phase `parity` of an mbarrier; false if it gave up.
-__device__ __forceinline__ bool tma_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false if it gave up
+// (after limit_ns of the global timer, or kTWaitPolls polls).
+__device__ __forceinline__ bool tma_wait(uint64_t* bar, uint32_t parity,
+                                         unsigned long long limit_ns = kTWaitNs) {
     const uint32_t b = smem_addr(bar);
-    for (long long i = 0; i < kTWaitLimit; ++i) {
+    const unsigned long long t0 = global_ns();
+    for (long long i = 0; i < kTWaitPolls; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -98,18 +118,21 @@ __device__ __forceinline__ bool tma_wait(uint64_t* bar, uint32_t parity) {
             : "r"(b), "r"(parity)
             : "memory");
         if (done) return true;
+        if ((i & 31) == 31 && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
 
-template <bool EPS_FIELD, bool TAU1>
-__global__ void __launch_bounds__(kTBand, kTBlocks)
+// step: the step number (the stochastic rounding of FP16 stores draws from it).
+template <class S, bool EPS_FIELD, bool TAU1>
+__global__ void __launch_bounds__(kTBand, TmaLayout<S>::blocks)
 k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUtensorMap tm,
-           const float* __restrict__ src, float* __restrict__ dst, int rows) {
+           const S* __restrict__ src, S* __restrict__ dst, int rows, uint32_t step) {
+    using L = TmaLayout<S>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-    float* stage = reinterpret_cast<float*>(base);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)kTRows * kTSlot * sizeof(float));
+    S* stage = reinterpret_cast<S*>(base);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)kTRows * L::slot * sizeof(S));
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * kTBand;
@@ -127,18 +150,22 @@ k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUte
     asm volatile("griddepcontrol.wait;" ::: "memory");
     // output row r lands in slot r - yb (each slot and barrier is used once)
     if (tid == 0)
-        for (int r = yb; r < ye; ++r) tma_load_slot(&tm, stage + (r - yb) * kTSlot, bar + (r - yb), x0 - kTHalo, r);
+        for (int r = yb; r < ye; ++r)
+            tma_load_slot(&tm, stage + (r - yb) * L::slot, bar + (r - yb), x0 - L::halo, r);
     // wall nodes of the segment, in parallel, while those loads fly
     if (x < k.nx) {
-        if (y0 == 0) wall_update(k, src, dst, x, 0, 0u);
-        if (y1 == k.ny) wall_update(k, src, dst, x, k.ny - 1, 0u);
+        if (y0 == 0) wall_update(k, src, dst, x, 0, step);
+        if (y1 == k.ny) wall_update(k, src, dst, x, k.ny - 1, step);
     }
     if (x0 == 0)
-        for (int y = yb + tid; y < ye; y += kTBand) wall_update(k, src, dst, 0, y, 0u);
+        for (int y = yb + tid; y < ye; y += kTBand) wall_update(k, src, dst, 0, y, step);
     if (x0 <= k.nx - 1 && k.nx - 1 < x0 + kTBand)
-        for (int y = yb + tid; y < ye; y += kTBand) wall_update(k, src, dst, k.nx - 1, y, 0u);
+        for (int y = yb + tid; y < ye; y += kTBand) wall_update(k, src, dst, k.nx - 1, y, step);
     const bool active = x >= 1 && x <= k.nx - 2;
-    const int c = tid + kTHalo;
+    const int c = tid + L::halo;
+    // FP16 storage at tau = 1 folds its scale into the collision weights, as
+    // the global-load kernel does
+    constexpr bool prescale = TAU1 && std::is_same<S, __half>::value;
     // every decision to go on is taken by the whole block (__syncthreads_and),
     // so no thread can leave the loop while others wait at a barrier
     bool ok = true;
@@ -146,21 +173,28 @@ k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUte
         ok = __syncthreads_and(tma_wait(bar + (y - yb), 0u));
         if (!ok) break;
         if (active) {
-            const float* sl = stage + (y - yb) * kTSlot + c;
+            const S* sl = stage + (y - yb) * L::slot + c;
             float f[9], h[9];
 #pragma unroll
-            for (int i = 1; i < 9; ++i) f[i] = sl[(i - 1) * kTPlane + plane_dx(i - 1)];
+            for (int i = 1; i < 9; ++i) f[i] = load_pop<S, float>(sl + ((i - 1) * L::plane + plane_dx(i - 1)), k.scale);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) h[i] = sl[(8 + i) * kTPlane + plane_dx(8 + i)];
+            for (int i = 0; i < 9; ++i) h[i] = load_pop<S, float>(sl + ((8 + i) * L::plane + plane_dx(8 + i)), k.scale);
             float fo[9], ho[9];
+            auto collide = [&](const KConst<float>& kk) {
+                const FastState<float> st = fast_moments(kk, f, h, y);
+                if constexpr (TAU1) fast_collide<float, true>(kk, st, f, h, fo, ho, prescale ? kk.inv_scale : 1.0f);
+                else fast_collide<float, false>(kk, st, f, h, fo, ho);
+            };
             if constexpr (EPS_FIELD) {
                 KConst<float> kc = k;
                 apply_eps(kc, node_eps(k, x, y));
-                fast_collide<float, TAU1>(kc, fast_moments(kc, f, h, y), f, h, fo, ho);
+                collide(kc);
             } else {
-                fast_collide<float, TAU1>(k, fast_moments(k, f, h, y), f, h, fo, ho);
+                collide(k);
             }
-            store_planes<float, float>(dst + (y * k.pitch + x), k.plane32, fo, ho, 1.0f, nullptr);
+            const int at = y * k.pitch + x;
+            Dither dither((uint32_t)at, step);
+            store_planes<S, float>(dst + at, k.plane32, fo, ho, prescale ? 1.0f : k.inv_scale, &dither);
         }
     }
     if (!ok && tid == 0) {
@@ -170,9 +204,33 @@ k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUte
     }
 }
 
+// Self-test of the bounded wait: an mbarrier that nothing arrives on, waited
+// on with a 20 ms limit; the wait gives up and sets the timeout bit of the
+// flag, exactly as a step whose copies never landed would.
+__global__ void k_wait_selftest(int* flag) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = __syncthreads_and(tma_wait(&bar, 0u, 20000000ull));
+    if (!ok && threadIdx.x == 0) atomicOr(flag, 2);
+}
+
+cudaError_t launch_wait_selftest(int* flag, cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(flag);
+    return cudaGetLastError();
+}
+
+template <class S> struct TmaType;
+template <> struct TmaType<float> { static constexpr CUtensorMapDataType value = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; };
+template <> struct TmaType<__half> { static constexpr CUtensorMapDataType value = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; };
+
 // The tensor map of one population buffer: dims (x: nx, y: ny, plane: 17),
-// box (136, 1, 1), zero fill outside.
-bool make_step_tensor_map(const KConst<float>& k, const float* buf, CUtensorMap* out) {
+// box (128 + 2 halo, 1, 1), zero fill outside.
+template <class S>
+bool make_step_tensor_map(const KConst<float>& k, const S* buf, CUtensorMap* out) {
     using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -186,10 +244,10 @@ bool make_step_tensor_map(const KConst<float>& k, const float* buf, CUtensorMap*
         encode = reinterpret_cast<Encode>(fn);
     }
     const cuuint64_t dims[3] = {(cuuint64_t)k.nx, (cuuint64_t)k.ny, (cuuint64_t)NPLANES};
-    const cuuint64_t strides[2] = {(cuuint64_t)k.pitch * sizeof(float), (cuuint64_t)k.plane * sizeof(float)};
-    const cuuint32_t box[3] = {(cuuint32_t)kTBox, 1u, 1u};
+    const cuuint64_t strides[2] = {(cuuint64_t)k.pitch * sizeof(S), (cuuint64_t)k.plane * sizeof(S)};
+    const cuuint32_t box[3] = {(cuuint32_t)TmaLayout<S>::box, 1u, 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
-    return encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(buf), dims, strides, box, estr,
+    return encode(out, TmaType<S>::value, 3, const_cast<S*>(buf), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -204,35 +262,37 @@ int tma_rows_default(const KConst<float>&) { return kTRows; }
 
 // Slots beyond the default 48 KB of dynamic shared memory need the
 // function's opt-in, once per device.
-template <bool E, bool T>
+template <class S, bool E, bool T>
 static cudaError_t allow_tma_smem() {
-    if (kTSmem <= 48 * 1024) return cudaSuccess;
+    if (TmaLayout<S>::smem <= 48 * 1024) return cudaSuccess;
     constexpr int kMaxDev = 64;
     static bool done[kMaxDev] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < kMaxDev && done[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_step_tma<E, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmem);
+    e = cudaFuncSetAttribute(k_step_tma<S, E, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TmaLayout<S>::smem);
     if (e == cudaSuccess && dev < kMaxDev) done[dev] = true;
     return e;
 }
 
-template <bool E, bool T>
+template <class S, bool E, bool T>
 static cudaError_t launch_tma(const cudaLaunchConfig_t& cfg, const KConst<float>& k, const CUtensorMap& tm,
-                              const float* src, float* dst, int rows) {
-    cudaError_t e = allow_tma_smem<E, T>();
+                              const S* src, S* dst, int rows, uint32_t step) {
+    cudaError_t e = allow_tma_smem<S, E, T>();
     if (e != cudaSuccess) return e;
-    return cudaLaunchKernelEx(&cfg, k_step_tma<E, T>, k, tm, src, dst, rows);
+    return cudaLaunchKernelEx(&cfg, k_step_tma<S, E, T>, k, tm, src, dst, rows, step);
 }
 
-cudaError_t launch_step_tma(const KConst<float>& k, const CUtensorMap& tm, const float* src, float* dst, int rows,
-                            cudaStream_t st) {
+template <class S>
+cudaError_t launch_step_tma(const KConst<float>& k, const CUtensorMap& tm, const S* src, S* dst, int rows,
+                            uint32_t step, cudaStream_t st) {
     if (rows < 1 || rows > kTRows) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((k.nx + kTBand - 1) / kTBand), (unsigned)((k.ny + rows - 1) / rows));
     cfg.blockDim = dim3(kTBand);
-    cfg.dynamicSmemBytes = kTSmem;
+    cfg.dynamicSmemBytes = TmaLayout<S>::smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -241,8 +301,17 @@ cudaError_t launch_step_tma(const KConst<float>& k, const CUtensorMap& tm, const
     cfg.numAttrs = 1;
     const bool tau1 = k.omf == 0.f && k.omT == 0.f;
     if (k.eps_field)
-        return tau1 ? launch_tma<true, true>(cfg, k, tm, src, dst, rows) : launch_tma<true, false>(cfg, k, tm, src, dst, rows);
-    return tau1 ? launch_tma<false, true>(cfg, k, tm, src, dst, rows) : launch_tma<false, false>(cfg, k, tm, src, dst, rows);
+        return tau1 ? launch_tma<S, true, true>(cfg, k, tm, src, dst, rows, step)
+                    : launch_tma<S, true, false>(cfg, k, tm, src, dst, rows, step);
+    return tau1 ? launch_tma<S, false, true>(cfg, k, tm, src, dst, rows, step)
+                : launch_tma<S, false, false>(cfg, k, tm, src, dst, rows, step);
 }
+
+template bool make_step_tensor_map<float>(const KConst<float>&, const float*, CUtensorMap*);
+template bool make_step_tensor_map<__half>(const KConst<float>&, const __half*, CUtensorMap*);
+template cudaError_t launch_step_tma<float>(const KConst<float>&, const CUtensorMap&, const float*, float*, int,
+                                            uint32_t, cudaStream_t);
+template cudaError_t launch_step_tma<__half>(const KConst<float>&, const CUtensorMap&, const __half*, __half*, int,
+                                             uint32_t, cudaStream_t);
 
 }  // namespace lbm

@@ -31,7 +31,8 @@ EXPORTED = ("lbm_params_default", "lbm_derived", "lbm_workspace_size", "lbm_crea
             "lbm_batch_autotune", "lbm_batch_set_launch", "lbm_batch_sync", "lbm_batch_nusselt",
             "lbm_batch_moments", "lbm_batch_steps_done", "lbm_batch_kernel_launches",
             "lbm_adjoint", "lbm_totals", "lbm_checkpoint", "lbm_set_force_profile",
-            "lbm_stream_function", "lbm_set_moment_segments")
+            "lbm_stream_function", "lbm_set_moment_segments", "lbm_wait_selftest",
+            "lbm_set_step_staging", "lbm_step_staged")
 BATCH_MODE = {"fused": 0, "graph": 1, "per_case": 2}
 
 
@@ -86,6 +87,10 @@ def load(build_if_missing: bool = True):
     L.lbm_set_fields.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
     L.lbm_step.argtypes = [H, C.c_int64]
     L.lbm_sync.argtypes = [H]
+    L.lbm_wait_selftest.argtypes = [H]
+    L.lbm_set_step_staging.argtypes = [H, C.c_int32]
+    L.lbm_step_staged.argtypes = [H]
+    L.lbm_step_staged.restype = C.c_int32
     L.lbm_moments.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
     L.lbm_nusselt.argtypes = [H, C.c_int, dp, C.c_void_p]
     L.lbm_residual.argtypes = [H, dp, dp]
@@ -120,7 +125,7 @@ def load(build_if_missing: bool = True):
     L.lbm_batch_kernel_launches.argtypes = [B]
     L.lbm_batch_kernel_launches.restype = C.c_int64
     for name in EXPORTED:
-        if name not in ("lbm_destroy", "lbm_last_error", "lbm_steps_done", "lbm_kernel_launches",
+        if name not in ("lbm_destroy", "lbm_last_error", "lbm_steps_done", "lbm_kernel_launches", "lbm_step_staged",
                         "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_steps_done",
                         "lbm_batch_kernel_launches"):
             getattr(L, name).restype = C.c_int
@@ -258,6 +263,20 @@ class Lattice:
 
     def sync(self):
         _check(self.lib.lbm_sync(self.h), self.h)
+
+    @property
+    def staged(self) -> bool:
+        """Whether the next step uses the kernel with TMA-staged rows."""
+        return bool(self.lib.lbm_step_staged(self.h))
+
+    @staged.setter
+    def staged(self, on: bool):
+        _check(self.lib.lbm_set_step_staging(self.h, int(bool(on))), self.h)
+
+    def wait_selftest(self):
+        """Launch the failure-detection self-test: a bounded device-side
+        wait that must give up; the next sync raises LBM_ERR_TIMEOUT."""
+        _check(self.lib.lbm_wait_selftest(self.h), self.h)
 
     def moments(self) -> dict:
         shape = (self.ny, self.nx)

@@ -1,10 +1,12 @@
-"""The FP32 step with TMA-staged rows (lattices walled on all four sides).
+"""The step with TMA-staged rows (FP32 and FP16 storage, lattices walled on
+all four sides).
 
-A single FP32 lattice walled on every side runs the staged kernel; a batch
-runs the same per-node code with plain global loads.  The two must agree
-bit for bit on lattices that span several 128-column bands and row segments
-with ragged edges at tau = 1; away from tau = 1 (with sources) and with a
-porosity field the staged kernel is checked against the FP64 oracle."""
+The staged kernel and the global-load kernel run the same per-node code: at
+tau = 1 they must agree bit for bit, for FP32 and FP16 storage, on lattices
+that span several 128-column bands and 4-row segments with ragged edges, and
+on the smallest lattices the staged kernel takes; the FP32 staged lattice
+also matches the batched kernel.  Away from tau = 1 (with sources) and with
+a porosity field the staged kernel is checked against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -16,48 +18,102 @@ from oracle_states import stored_state
 
 pytestmark = pytest.mark.gpu
 
+SIZES = [(300, 250), (129, 517), (4, 4), (131, 5), (517, 9)]
 
-def _bitwise_against_batch(p, steps, seed):
-    T, ux, uy = W.random_fields(p, seed=seed, amp_u=2e-3, amp_T=0.3)
-    g = lbm.Lattice(p, "f32")
-    g.set_fields(T, ux, uy)
+
+def _run(p, precision, fields, steps, staged):
+    g = lbm.Lattice(p, precision)
+    g.set_fields(*fields)
+    if not staged:
+        g.staged = False
+    assert g.staged == staged
     g.step(steps)
     g.sync()
-    b = lbm.Batch([p], "f32")
-    b.set_fields(0, T, ux, uy)
-    b.step(steps, "fused")
-    b.sync()
-    mg, mb = g.moments(), b.moments(0)
-    for k in ("ux", "uy", "T", "p"):
-        assert np.array_equal(mg[k], mb[k]), k
-    assert np.all(np.isfinite(mg["T"]))
-    b.close()
+    return g
 
 
-@pytest.mark.parametrize("nx,ny", [(300, 250), (129, 517), (4, 4), (131, 5), (517, 9)])
-def test_staged_step_matches_global_loads(nx, ny):
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+@pytest.mark.parametrize("nx,ny", SIZES)
+def test_staged_step_matches_global_loads(precision, nx, ny):
     """Several bands and segments, ragged last band and segment, and the
     smallest lattices the staged kernel takes (4 rows, one partial band)."""
-    _bitwise_against_batch(W.cavity(nx, 1e5, 1e-3, 0.5, ny=ny), 60, seed=nx + ny)
+    p = W.cavity(nx, 1e5, 1e-3, 0.5, ny=ny)
+    fields = W.random_fields(p, seed=nx + ny, amp_u=2e-3, amp_T=0.3)
+    a = _run(p, precision, fields, 60, True)
+    b = _run(p, precision, fields, 60, False)
+    fa, ga = a.get_state()
+    fb, gb = b.get_state()
+    assert np.array_equal(fa[1:], fb[1:]) and np.array_equal(ga, gb)
+    ma = a.moments()
+    assert np.all(np.isfinite(ma["T"]))
+    if precision == "f32":
+        bt = lbm.Batch([p], "f32")
+        bt.set_fields(0, *fields)
+        bt.step(60, "fused")
+        bt.sync()
+        mb = bt.moments(0)
+        for k in ("ux", "uy", "T", "p"):
+            assert np.array_equal(ma[k], mb[k]), k
+        bt.close()
 
 
-def test_staged_step_off_tau_one_with_sources():
-    """tau_f, tau_T != 1 (the general collision) with an internal heat
-    source, a body force and Dirichlet walls on all four sides: one step from
-    an oracle-made FP32 state against the oracle on every node, at FP32
-    rounding.  (The general collision's products may contract into fused
-    multiply-adds differently in the two kernels, so this case is not
-    compared bit for bit.)"""
-    p = W.cavity(260, 1e5, 1e-3, 0.45, ny=140, tau_f=0.8, tau_T=1.15, Q=1e-4, ax=1e-7,
-                 bc=("dirichlet",) * 4, T_bc=(1.0, 0.0, 0.7, 0.2))
-    o, f0, g0 = stored_state(p, W.random_fields(p, seed=3, amp_u=2e-3, amp_T=0.3), "f32", steps=1)
-    g = lbm.Lattice(p, "f32")
+def test_staging_switch_is_refused_where_unavailable():
+    per = lbm.Lattice(W.poiseuille(nx=16, ny=32), "f32")
+    assert not per.staged
+    with pytest.raises(lbm.LbmError):
+        per.staged = True
+    f64 = lbm.Lattice(W.cavity(32, 1e4, 1e-2, 0.6), "f64")
+    assert not f64.staged
+    with pytest.raises(lbm.LbmError):
+        f64.staged = True
+    g = lbm.Lattice(W.cavity(32, 1e4, 1e-2, 0.6), "f16")
+    assert g.staged
+    g.staged = False
+    g.staged = True
+    assert g.staged
+
+
+def _off_tau_problem():
+    return W.cavity(260, 1e5, 1e-3, 0.45, ny=140, tau_f=0.8, tau_T=1.15, Q=1e-4, ax=1e-7,
+                    bc=("dirichlet",) * 4, T_bc=(1.0, 0.0, 0.7, 0.2))
+
+
+def test_staged_step_off_tau_one_matches_global_loads():
+    """The general collision (tau != 1) with a heat source and a body force,
+    FP32: staged and global-load kernels agree to FP32 rounding after 5 steps
+    (their products may contract into fused multiply-adds differently)."""
+    p = _off_tau_problem()
+    fields = W.random_fields(p, seed=8, amp_u=2e-3, amp_T=0.3)
+    fa, ga = _run(p, "f32", fields, 5, True).get_state()
+    fb, gb = _run(p, "f32", fields, 5, False).get_state()
+    assert np.abs(fa[1:] - fb[1:]).max() <= 1e-6 * np.abs(fb[1:]).max()
+    assert np.abs(ga - gb).max() <= 1e-6 * np.abs(gb).max()
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_staged_step_off_tau_one_against_oracle(precision):
+    """tau_f 0.8, tau_T 1.15 with an internal heat source, a body force and
+    Dirichlet walls on all four sides: one staged step from an oracle-made
+    state in the storage precision against the oracle on every node (FP32:
+    1e-6 of the population scale; FP16: one FP16 step of each value, the
+    thermal populations as deviations from w_i sigma T0)."""
+    p = _off_tau_problem()
+    o, f0, g0 = stored_state(p, W.random_fields(p, seed=3, amp_u=2e-3, amp_T=0.3), precision, steps=1)
+    g = lbm.Lattice(p, precision)
+    assert g.staged
     g.set_state(f0, g0)
     g.step(1)
     f1, g1 = g.get_state()
     o.run(1)
-    assert np.abs(f1[1:] - o.f[1:]).max() <= 1e-6 * np.abs(o.f[1:]).max()
-    assert np.abs(g1 - o.g).max() <= 1e-6 * np.abs(o.g).max()
+    if precision == "f32":
+        assert np.abs(f1[1:] - o.f[1:]).max() <= 1e-6 * np.abs(o.f[1:]).max()
+        assert np.abs(g1 - o.g).max() <= 1e-6 * np.abs(o.g).max()
+    else:
+        fo = o.f[1:]
+        assert np.all(np.abs(f1[1:] - fo) <= 2.0 ** -10 * np.abs(fo) + 1e-6 * np.abs(fo).max())
+        w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+        dev = np.abs(o.g - w * p["sigma"] * oracle.derived(p)["T0"])
+        assert np.all(np.abs(g1 - o.g) <= 2.0 ** -10 * dev + 1e-6 * dev.max())
 
 
 def test_staged_step_porosity_field_against_oracle():
@@ -77,3 +133,27 @@ def test_staged_step_porosity_field_against_oracle():
     du = np.sqrt((mg["ux"] - mo["ux"]) ** 2 + (mg["uy"] - mo["uy"]) ** 2)
     un = np.sqrt(mo["ux"] ** 2 + mo["uy"] ** 2)
     assert np.linalg.norm(du) / np.linalg.norm(un) <= 1e-3
+
+
+def test_bounded_wait_gives_up_and_reports_timeout():
+    """Failure detection without a fault: a wait on an mbarrier that nothing
+    arrives on gives up after its time limit, the host reads LBM_ERR_TIMEOUT
+    (sticky), and after lbm_set_fields the same context steps normally and
+    matches a fresh lattice bit for bit."""
+    p = W.cavity(200, 1e5, 1e-3, 0.5, ny=64)
+    g = lbm.Lattice(p, "f32")
+    g.step(3)
+    g.wait_selftest()
+    with pytest.raises(lbm.LbmError) as e:
+        g.sync()
+    assert e.value.status == -4
+    with pytest.raises(lbm.LbmError) as e:
+        g.step(1)
+    assert e.value.status == -4
+    g.set_fields()
+    g.step(20)
+    g.sync()
+    ref = lbm.Lattice(p, "f32")
+    ref.step(20)
+    ref.sync()
+    assert np.array_equal(g.moments()["T"], ref.moments()["T"])
