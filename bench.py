@@ -310,8 +310,9 @@ def adjoint_line(device, local) -> dict:
 def batch_line(device, local, peak: float) -> dict:
     """512 independent cavities (sizes 64..512, Ra log-uniform in [1e3, 1e6],
     Da log-uniform in [1e-6, 1e-2], eps uniform in [0.3, 0.9]), FP32: the
-    autotuned fused step replayed from a CUDA graph, the same launches
-    without the graph, and one single-lattice launch per cavity."""
+    staged fused step replayed from a CUDA graph, the same launches without
+    the graph, one single-lattice launch per cavity, and the autotuned
+    global-load kernel replayed from a graph."""
     import torch
 
     from paper_1505_02976_gb300 import lbm
@@ -319,11 +320,10 @@ def batch_line(device, local, peak: float) -> dict:
     probs = W.batch_cavities(512)
     stream = torch.cuda.Stream(device)
     b = lbm.Batch(probs, "f32", device=local, stream=stream)
-    tile_x, grid = b.autotune(3)
     cells = b.cells
-    res = {"cavities": len(probs), "nodes": cells, "tile_x": tile_x, "grid": grid, "unit": "MLUPS",
-           "dtype": "f32"}
-    for mode, steps in (("graph", 100), ("fused", 100), ("per_case", 10)):
+    res = {"cavities": len(probs), "nodes": cells, "unit": "MLUPS", "dtype": "f32", "staged": b.staged}
+
+    def timed(mode, steps, key):
         b.step(2 if mode != "graph" else 50, mode)
         b.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -332,7 +332,16 @@ def batch_line(device, local, peak: float) -> dict:
         e1.record(stream)
         e1.synchronize()
         sec = e0.elapsed_time(e1) / 1e3
-        res[mode] = cells * steps / sec / 1e6
+        res[key] = cells * steps / sec / 1e6
+        return sec
+
+    if b.staged:
+        b.staged = False
+        res["tile_x"], res["grid"] = b.autotune(3)
+        timed("graph", 100, "graph_global_loads")
+        b.staged = True
+    for mode, steps in (("graph", 100), ("fused", 100), ("per_case", 10)):
+        sec = timed(mode, steps, mode)
         if mode == "graph":
             res["hbm_frac_graph"] = BYTES_PER_CELL["f32"] * cells * steps / sec / 1e9 / peak
     b.sync()

@@ -353,13 +353,31 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t n, int mode);
 /* Pick the tile width (32, 64 or 128 nodes; tiles hold 128 nodes) and the
  * grid size (1, 2 or 4 waves of resident blocks) of the fused step by timing
  * steps_per_candidate + 1 steps of each candidate.  These are real steps of
- * the run (every launch shape computes identical values).  Synchronises. */
+ * the run (every launch shape computes identical values).  The launch shape
+ * belongs to the global-load kernel; a staged batch (below) times the same
+ * kernel for every candidate.  Synchronises. */
 lbm_status lbm_batch_autotune(lbm_batch* b, int32_t steps_per_candidate, int32_t* tile_x, int32_t* grid);
 
-/* Set the fused step's launch shape explicitly. */
+/* Set the fused step's launch shape explicitly (global-load kernel). */
 lbm_status lbm_batch_set_launch(lbm_batch* b, int32_t tile_x, int32_t grid);
 
-/* Wait for the stream; LBM_ERR_NONFINITE if any cavity produced a NaN/Inf. */
+/* Step kernel of a batch (no counterpart in the paper; a launch choice).
+ * A batch of FP32 cavities that are all walled on all four sides (each at
+ * least 4 x 4) defaults to staged rows: one block per band of 128 columns x
+ * 4 rows of one cavity loads the planes its rows pull from with tensor
+ * copies (the maps of every cavity live in the workspace) and waits on them
+ * with bounded waits, in every mode (per-case mode launches the single-
+ * lattice staged kernel per cavity).  staged = 0 selects the global-load
+ * kernel and its launch shape; staged = 1 restores staging (LBM_ERR_ARG
+ * where it is unavailable).  Both run the same per-node arithmetic (bit for
+ * bit at tau_f = tau_T = 1).  lbm_batch_staged returns 1 when the next
+ * step uses staged rows, else 0. */
+lbm_status lbm_batch_set_staging(lbm_batch* b, int32_t staged);
+int32_t lbm_batch_staged(const lbm_batch* b);
+
+/* Wait for the stream; LBM_ERR_TIMEOUT if a bounded wait of the staged
+ * kernel gave up, else LBM_ERR_NONFINITE if any cavity produced a NaN/Inf
+ * (both sticky until lbm_batch_set_fields). */
 lbm_status lbm_batch_sync(lbm_batch* b);
 
 /* Mean Nusselt number of every cavity on one side (as lbm_nusselt), into

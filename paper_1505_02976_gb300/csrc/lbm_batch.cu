@@ -46,7 +46,14 @@ struct lbm_batch {
     int tile_x, grid;                  // chosen launch shape
     int sms;
     int64_t steps, launches;
-    bool nonfinite;
+    bool nonfinite, timeout;
+    // FP32 batches of cavities walled on all four sides: the staged kernel
+    // (one block per 128-column x 4-row item), its work list and the tensor
+    // maps of every cavity in both buffers (device: maps[buffer * n + c])
+    bool staged, staged_ready;
+    size_t off_maps, off_sitems;
+    int n_sitems;
+    std::vector<CUtensorMap> hmaps[2];
     cudaGraphExec_t graph[2];          // captured kGraphChunk steps, one per starting buffer
     int graph_tile, graph_grid;
     std::string err;
@@ -57,6 +64,8 @@ struct lbm_batch {
     int* flag() const { return (int*)(ws + off_flag); }
     const lbm::BatchItem* items(int t) const { return (const lbm::BatchItem*)(ws + off_items[t]); }
     int* bounds() const { return (int*)(ws + off_bounds); }
+    const CUtensorMap* maps(int buffer) const { return (const CUtensorMap*)(ws + off_maps) + (size_t)buffer * n; }
+    const lbm::BatchItem* sitems() const { return (const lbm::BatchItem*)(ws + off_sitems); }
     size_t es() const { return precision == LBM_F64 ? 8 : 4; }
 };
 
@@ -116,6 +125,27 @@ std::vector<lbm::BatchItem> make_items(const std::vector<lbm_params>& prm, int t
     return v;
 }
 
+// Whether every cavity can take the staged kernel (FP32, walled on all four
+// sides, at least 4 x 4 nodes).
+bool stageable(const std::vector<lbm_params>& prm) {
+    for (const lbm_params& p : prm) {
+        if (p.precision != LBM_F32 || p.nx < 4 || p.ny < 4) return false;
+        for (int q = 0; q < 4; ++q)
+            if (p.bc[q] == LBM_BC_PERIODIC) return false;
+    }
+    return true;
+}
+
+// Work items of the staged kernel: every cavity's bands of 128 columns x
+// segments of `rows` rows, cavity by cavity.
+std::vector<lbm::BatchItem> make_staged_items(const std::vector<lbm_params>& prm, int rows) {
+    std::vector<lbm::BatchItem> v;
+    for (int c = 0; c < (int)prm.size(); ++c)
+        for (int y0 = 0; y0 < prm[c].ny; y0 += rows)
+            for (int x0 = 0; x0 < prm[c].nx; x0 += 128) v.push_back({c, x0, y0, 2});
+    return v;
+}
+
 // Block ranges of equal estimated cost: bounds[k] is the first item of block k.
 std::vector<int> make_bounds(const std::vector<double>& cum, int grid) {
     const int n = (int)cum.size() - 1;
@@ -164,6 +194,15 @@ lbm_status batch_layout(const lbm_params* p, int n, lbm_batch* b, std::string* w
         o += align256((size_t)b->n_items[t] * sizeof(lbm::BatchItem));
     }
     b->off_bounds = o; o += align256((size_t)(kMaxGrid + 1) * sizeof(int));
+    b->n_sitems = 0;
+    b->off_maps = b->off_sitems = o;
+    if (stageable(b->prm)) {
+        const size_t ns = make_staged_items(b->prm, lbm::tma_batch_rows()).size();
+        if (ns >= (size_t)1 << 31) { *why = "batch too large"; return LBM_ERR_ARG; }
+        b->n_sitems = (int)ns;
+        b->off_maps = o; o += align256((size_t)2 * n * sizeof(CUtensorMap));
+        b->off_sitems = o; o += align256(ns * sizeof(lbm::BatchItem));
+    }
     b->off_fields = o; o += align256(4 * b->max_cells * sizeof(double));
     b->off_nu = o; o += align256((size_t)n * sizeof(double));
     b->off_flag = o; o += 256;
@@ -213,6 +252,10 @@ cudaError_t set_bounds(lbm_batch* b, int tile_x, int grid) {
 cudaError_t fused_step(lbm_batch* b, int tile_x, int grid) {
     const int t = tile_index(tile_x);
     const int src = b->cur, dst = 1 - b->cur;
+    if (b->staged)
+        return lbm::launch_step_batch_tma((const lbm::BatchCavity<float>*)(b->ws + b->off_cav), b->maps(src),
+                                          b->sitems(), b->n_sitems, (const float*)b->buf(src), (float*)b->buf(dst),
+                                          (uint32_t)b->steps, b->stream);
     cudaError_t e = set_bounds(b, tile_x, grid);
     if (e != cudaSuccess) return e;
     return bdispatch(b, [&](auto* dcav, auto&, auto* tag) {
@@ -224,6 +267,16 @@ cudaError_t fused_step(lbm_batch* b, int tile_x, int grid) {
 
 cudaError_t per_case_step(lbm_batch* b) {
     const int src = b->cur, dst = 1 - b->cur;
+    if (b->staged) {
+        for (int c = 0; c < b->n; ++c) {
+            const long long o = b->cav32[c].offset;
+            cudaError_t e = lbm::launch_step_tma(b->cav32[c].k, b->hmaps[src][c], (const float*)b->buf(src) + o,
+                                                 (float*)b->buf(dst) + o, lbm::tma_batch_rows(), (uint32_t)b->steps,
+                                                 b->stream);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     return bdispatch(b, [&](auto*, auto& hc, auto* tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         for (int c = 0; c < b->n; ++c) {
@@ -314,7 +367,8 @@ lbm_status lbm_batch_create(const lbm_params* p, int32_t n, void* stream, void* 
     }
     b->cur = 0;
     b->steps = b->launches = 0;
-    b->nonfinite = false;
+    b->nonfinite = b->timeout = false;
+    b->staged = b->staged_ready = false;
     b->graph[0] = b->graph[1] = nullptr;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -336,6 +390,24 @@ lbm_status lbm_batch_create(const lbm_params* p, int32_t n, void* stream, void* 
         std::vector<lbm::BatchItem> it = make_items(b->prm, kTiles[t], nullptr);
         s = upload(b->off_items[t], it.data(), it.size() * sizeof(lbm::BatchItem), "work list");
         if (s == LBM_OK) s = (cudaStreamSynchronize(b->stream) == cudaSuccess) ? LBM_OK : LBM_ERR_CUDA;
+    }
+    if (s == LBM_OK && b->n_sitems > 0) {
+        bool ok = true;
+        for (int i = 0; i < 2; ++i) {
+            b->hmaps[i].resize(n);
+            for (int c = 0; c < n && ok; ++c)
+                ok = lbm::make_step_tensor_map(b->cav32[c].k, (const float*)b->buf(i) + b->cav32[c].offset,
+                                               &b->hmaps[i][c]);
+        }
+        if (ok) {
+            std::vector<lbm::BatchItem> it = make_staged_items(b->prm, lbm::tma_batch_rows());
+            s = upload(b->off_sitems, it.data(), it.size() * sizeof(lbm::BatchItem), "staged work list");
+            for (int i = 0; i < 2 && s == LBM_OK; ++i)
+                s = upload(b->off_maps + (size_t)i * n * sizeof(CUtensorMap), b->hmaps[i].data(),
+                           (size_t)n * sizeof(CUtensorMap), "tensor maps");
+            if (s == LBM_OK) s = (cudaStreamSynchronize(b->stream) == cudaSuccess) ? LBM_OK : LBM_ERR_CUDA;
+            b->staged = b->staged_ready = s == LBM_OK;
+        }
     }
     // default launch shape: 32-wide tiles, one wave of resident blocks
     b->tile_x = 32;
@@ -397,12 +469,13 @@ lbm_status lbm_batch_set_fields(lbm_batch* b, int32_t cavity, const double* T, c
     LBM_BCUDA(b, cudaMemsetAsync(b->flag(), 0, sizeof(int), b->stream), "flag reset");
     LBM_BCUDA(b, cudaStreamSynchronize(b->stream), "set_fields");
     if (cavity < 0) b->steps = 0;
-    b->nonfinite = false;
+    b->nonfinite = b->timeout = false;
     return LBM_OK;
 }
 
 lbm_status lbm_batch_step(lbm_batch* b, int64_t n, int mode) {
     if (!b || n < 0) return b ? bfail(b, LBM_ERR_ARG, "negative step count") : LBM_ERR_ARG;
+    if (b->timeout) return bfail(b, LBM_ERR_TIMEOUT, "a bounded wait of the staged step gave up");
     if (b->nonfinite) return bfail(b, LBM_ERR_NONFINITE, "non-finite velocity or temperature");
     if (mode < LBM_BATCH_FUSED || mode > LBM_BATCH_PER_CASE) return bfail(b, LBM_ERR_ARG, "unknown mode");
     if (mode == LBM_BATCH_GRAPH && b->stream == nullptr)
@@ -495,10 +568,23 @@ lbm_status lbm_batch_sync(lbm_batch* b) {
     LBM_BCUDA(b, cudaStreamSynchronize(b->stream), "stream synchronise");
     int flag = 0;
     LBM_BCUDA(b, cudaMemcpy(&flag, b->flag(), sizeof(int), cudaMemcpyDeviceToHost), "flag read");
-    if (flag) b->nonfinite = true;
+    if (flag & 2) b->timeout = true;
+    if (flag & 1) b->nonfinite = true;
+    if (b->timeout) return bfail(b, LBM_ERR_TIMEOUT, "a bounded wait of the staged step gave up");
     if (b->nonfinite) return bfail(b, LBM_ERR_NONFINITE, "non-finite velocity or temperature");
     return LBM_OK;
 }
+
+lbm_status lbm_batch_set_staging(lbm_batch* b, int32_t staged) {
+    if (!b) return LBM_ERR_ARG;
+    if (staged && !b->staged_ready)
+        return bfail(b, LBM_ERR_ARG, "staged rows need FP32 cavities walled on all sides");
+    if (b->staged != (staged != 0)) drop_graphs(b);
+    b->staged = staged != 0;
+    return LBM_OK;
+}
+
+int32_t lbm_batch_staged(const lbm_batch* b) { return b && b->staged ? 1 : 0; }
 
 lbm_status lbm_batch_nusselt(lbm_batch* b, int side, double* nu_mean) {
     if (!b || side < 0 || side > 3 || !nu_mean) return b ? bfail(b, LBM_ERR_ARG, "bad side or null output") : LBM_ERR_ARG;

@@ -32,6 +32,7 @@
 
 #include <type_traits>
 
+#include "lbm_internal.h"
 #include "lbm_step.cuh"
 
 namespace lbm {
@@ -123,20 +124,20 @@ __device__ __forceinline__ bool tma_wait(uint64_t* bar, uint32_t parity,
     return false;
 }
 
-// step: the step number (the stochastic rounding of FP16 stores draws from it).
+// One block of the staged step: columns x0 .. x0 + 127 and rows y0 ..
+// y0 + rows - 1 (rows <= kTRows) of the lattice k, whose population buffers
+// src / dst the tensor map tm describes.  step: the step number (the
+// stochastic rounding of FP16 stores draws from it).  smem_raw: the block's
+// dynamic shared memory (TmaLayout<S>::smem bytes).
 template <class S, bool EPS_FIELD, bool TAU1>
-__global__ void __launch_bounds__(kTBand, TmaLayout<S>::blocks)
-k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUtensorMap tm,
-           const S* __restrict__ src, S* __restrict__ dst, int rows, uint32_t step) {
+__device__ __forceinline__ void staged_block(const KConst<float>& k, const CUtensorMap* tm, const S* __restrict__ src,
+                                             S* __restrict__ dst, int x0, int y0, int rows, uint32_t step,
+                                             unsigned char* smem_raw) {
     using L = TmaLayout<S>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     S* stage = reinterpret_cast<S*>(base);
     uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)kTRows * L::slot * sizeof(S));
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * kTBand;
-    const int y0 = blockIdx.y * rows;
     const int y1 = min(y0 + rows, k.ny);
     const int yb = max(y0, 1), ye = min(y1, k.ny - 1);  // interior rows of the segment (at most kTRows)
     const int x = x0 + tid;
@@ -151,7 +152,7 @@ k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUte
     // output row r lands in slot r - yb (each slot and barrier is used once)
     if (tid == 0)
         for (int r = yb; r < ye; ++r)
-            tma_load_slot(&tm, stage + (r - yb) * L::slot, bar + (r - yb), x0 - L::halo, r);
+            tma_load_slot(tm, stage + (r - yb) * L::slot, bar + (r - yb), x0 - L::halo, r);
     // wall nodes of the segment, in parallel, while those loads fly
     if (x < k.nx) {
         if (y0 == 0) wall_update(k, src, dst, x, 0, step);
@@ -202,6 +203,45 @@ k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUte
         // let this block's copies land before its shared memory is released
         for (int r = yb; r < ye; ++r) (void)tma_wait(bar + (r - yb), 0u);
     }
+}
+
+// The staged step of one lattice: block (bx, by) owns band bx and rows
+// by * rows .. by * rows + rows - 1.
+template <class S, bool EPS_FIELD, bool TAU1>
+__global__ void __launch_bounds__(kTBand, TmaLayout<S>::blocks)
+k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUtensorMap tm,
+           const S* __restrict__ src, S* __restrict__ dst, int rows, uint32_t step) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    staged_block<S, EPS_FIELD, TAU1>(k, &tm, src, dst, blockIdx.x * kTBand, blockIdx.y * rows, rows, step,
+                                     smem_raw);
+}
+
+// The staged step of a batch of FP32 cavities walled on all four sides: block
+// i takes work item i = (cavity, band origin x0, segment origin y0) of a list
+// sorted by cavity; the cavity's constants are staged in shared memory and
+// its tensor map (for the source buffer) is read from global memory.
+__global__ void __launch_bounds__(kTBand, TmaLayout<float>::blocks)
+k_step_batch_tma(const BatchCavity<float>* __restrict__ cav, const CUtensorMap* __restrict__ maps,
+                 const BatchItem* __restrict__ items, const float* __restrict__ src, float* __restrict__ dst,
+                 uint32_t step) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ KConst<float> ks;
+    __shared__ long long off;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // the descriptors and maps are written once, before any step: they may be
+    // read before the previous step has finished
+    const BatchItem w = items[blockIdx.x];
+    const int* from = reinterpret_cast<const int*>(&cav[w.cavity].k);
+    int* to = reinterpret_cast<int*>(&ks);
+    for (int q = threadIdx.x; q < (int)(sizeof(KConst<float>) / sizeof(int)); q += kTBand) to[q] = from[q];
+    if (threadIdx.x == 0) off = cav[w.cavity].offset;
+    __syncthreads();
+    const CUtensorMap* tm = maps + w.cavity;
+    if (ks.omf == 0.f && ks.omT == 0.f)
+        staged_block<float, false, true>(ks, tm, src + off, dst + off, w.a, w.b, kTRows, step, smem_raw);
+    else
+        staged_block<float, false, false>(ks, tm, src + off, dst + off, w.a, w.b, kTRows, step, smem_raw);
 }
 
 // Self-test of the bounded wait: an mbarrier that nothing arrives on, waited
@@ -306,6 +346,24 @@ cudaError_t launch_step_tma(const KConst<float>& k, const CUtensorMap& tm, const
     return tau1 ? launch_tma<S, false, true>(cfg, k, tm, src, dst, rows, step)
                 : launch_tma<S, false, false>(cfg, k, tm, src, dst, rows, step);
 }
+
+cudaError_t launch_step_batch_tma(const BatchCavity<float>* cav, const CUtensorMap* maps, const BatchItem* items,
+                                  int n_items, const float* src, float* dst, uint32_t step, cudaStream_t st) {
+    if (n_items < 1) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_items);
+    cfg.blockDim = dim3(kTBand);
+    cfg.dynamicSmemBytes = TmaLayout<float>::smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step_batch_tma, cav, maps, items, src, dst, step);
+}
+
+int tma_batch_rows() { return kTRows; }
 
 template bool make_step_tensor_map<float>(const KConst<float>&, const float*, CUtensorMap*);
 template bool make_step_tensor_map<__half>(const KConst<float>&, const __half*, CUtensorMap*);

@@ -32,7 +32,7 @@ EXPORTED = ("lbm_params_default", "lbm_derived", "lbm_workspace_size", "lbm_crea
             "lbm_batch_moments", "lbm_batch_steps_done", "lbm_batch_kernel_launches",
             "lbm_adjoint", "lbm_totals", "lbm_checkpoint", "lbm_set_force_profile",
             "lbm_stream_function", "lbm_set_moment_segments", "lbm_wait_selftest",
-            "lbm_set_step_staging", "lbm_step_staged")
+            "lbm_set_step_staging", "lbm_step_staged", "lbm_batch_set_staging", "lbm_batch_staged")
 BATCH_MODE = {"fused": 0, "graph": 1, "per_case": 2}
 
 
@@ -107,6 +107,9 @@ def load(build_if_missing: bool = True):
     L.lbm_stream_function.argtypes = [H, C.c_void_p, C.c_int, C.c_void_p]
     L.lbm_set_moment_segments.argtypes = [H, C.c_int32]
     B = C.c_void_p
+    L.lbm_batch_set_staging.argtypes = [B, C.c_int32]
+    L.lbm_batch_staged.argtypes = [B]
+    L.lbm_batch_staged.restype = C.c_int32
     L.lbm_batch_workspace_size.argtypes = [P, C.c_int32, C.POINTER(C.c_size_t)]
     L.lbm_batch_create.argtypes = [P, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(B)]
     L.lbm_batch_destroy.argtypes = [B]
@@ -125,7 +128,7 @@ def load(build_if_missing: bool = True):
     L.lbm_batch_kernel_launches.argtypes = [B]
     L.lbm_batch_kernel_launches.restype = C.c_int64
     for name in EXPORTED:
-        if name not in ("lbm_destroy", "lbm_last_error", "lbm_steps_done", "lbm_kernel_launches", "lbm_step_staged",
+        if name not in ("lbm_destroy", "lbm_last_error", "lbm_steps_done", "lbm_kernel_launches", "lbm_step_staged", "lbm_batch_staged",
                         "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_steps_done",
                         "lbm_batch_kernel_launches"):
             getattr(L, name).restype = C.c_int
@@ -427,6 +430,15 @@ class Batch:
 
     def sync(self):
         self._check(self.lib.lbm_batch_sync(self.h))
+
+    @property
+    def staged(self) -> bool:
+        """Whether the next step uses the kernel with TMA-staged rows."""
+        return bool(self.lib.lbm_batch_staged(self.h))
+
+    @staged.setter
+    def staged(self, on: bool):
+        self._check(self.lib.lbm_batch_set_staging(self.h, int(bool(on))))
 
     def nusselt(self, side="W"):
         k = SIDE[side] if isinstance(side, str) else int(side)

@@ -107,3 +107,68 @@ def test_batch_of_the_benchmark_distribution_runs():
     b.sync()
     nu = b.nusselt("W")
     assert np.all(np.isfinite(nu)) and np.all(nu > 0.5)
+
+
+def _walled_problems():
+    return [
+        W.cavity(20, 1e4, 1e-2, 0.6),
+        W.cavity(37, 1e5, 1e-3, 0.4, ny=29),
+        W.cavity(300, 1e6, 1e-4, 0.4, ny=131),
+        W.cavity(4, 1e4, 1e-2, 0.5, ny=6),
+        W.cavity(45, 3e5, 1e-4, 0.3, ny=70, bc=("dirichlet", "adiabatic", "dirichlet", "adiabatic"),
+                 T_bc=(1.0, 0.0, 0.8, 0.0)),
+        W.cavity(130, 1e5, 1e-3, 0.5, ny=50, tau_f=0.8, tau_T=1.1),
+    ]
+
+
+def test_staged_batch_matches_global_loads_and_single_lattices():
+    """An FP32 batch of walled cavities (one band and several, ragged bands and
+    segments, 4 x 6, tau != 1 in the last cavity) takes the staged kernel in
+    every mode: fused, graph and per-case runs, the global-load batch and
+    single lattices agree bit for bit at tau = 1, and to FP32 rounding for
+    the tau != 1 cavity (the kernels' products may contract differently)."""
+    probs = _walled_problems()
+    rng = np.random.Generator(np.random.PCG64(17))
+    fields = [W.random_fields(p, seed=int(rng.integers(1 << 30)), amp_u=2e-3, amp_T=0.3) for p in probs]
+    runs = {}
+    for mode, staged in (("fused", True), ("graph", True), ("per_case", True), ("fused", False)):
+        b = lbm.Batch(probs, "f32")
+        assert b.staged
+        b.staged = staged
+        for c, f in enumerate(fields):
+            b.set_fields(c, *f)
+        b.step(100, mode)
+        b.sync()
+        runs[(mode, staged)] = [b.moments(c) for c in range(len(probs))]
+        b.close()
+    ref = runs[("fused", True)]
+    singles = []
+    for c, p in enumerate(probs):
+        g = lbm.Lattice(p, "f32")
+        g.set_fields(*fields[c])
+        assert g.staged
+        g.step(100)
+        singles.append(g.moments())
+    for c, p in enumerate(probs):
+        tau1 = p["tau_f"] == 1.0 and p["tau_T"] == 1.0
+        others = [runs[k][c] for k in runs if k != ("fused", True)] + [singles[c]]
+        for m in others:
+            for k in ("ux", "uy", "T", "p"):
+                if tau1:
+                    assert np.array_equal(m[k], ref[c][k]), (c, k)
+                else:
+                    scale = max(np.abs(ref[c][k]).max(), 1e-12)
+                    assert np.abs(m[k] - ref[c][k]).max() <= 1e-5 * scale, (c, k)
+
+
+def test_staging_is_refused_for_fp64_and_periodic_batches():
+    b = lbm.Batch(_mixed_problems(), "f32")  # holds a periodic channel
+    assert not b.staged
+    with pytest.raises(lbm.LbmError):
+        b.staged = True
+    b.close()
+    b = lbm.Batch(_walled_problems()[:2], "f64")
+    assert not b.staged
+    with pytest.raises(lbm.LbmError):
+        b.staged = True
+    b.close()
