@@ -10,8 +10,9 @@
 // loaded (one 3-D tensor copy of 128 + 2 halo columns x 1 row x 1 plane)
 // from its own source row.  A block owns a band of 128 columns and a segment of up to
 // kTRows rows; one thread issues all of the block's copies (17 plane rows
-// per output row, 37 KB for 4 FP32 rows) at its start, and the threads wait on
-// each row's mbarrier instead of on their own global loads.  Many short
+// per output row, 37 KB for 4 FP32 rows) at its start, and each thread waits
+// on each row's mbarrier instead of on its own global loads (no block
+// barrier between rows: the slots are written once).  Many short
 // blocks keep the SMs busy to the end of the step (measured on the 2048^2
 // and 8192^2 FP32 cavities: 4-row segments beat 2, 3, 5, 6, 8, 16, 32 and
 // 64 rows streamed through a ring of 2 to 6 row slots, and the global-load
@@ -167,12 +168,16 @@ __device__ __forceinline__ void staged_block(const KConst<float>& k, const CUten
     // FP16 storage at tau = 1 folds its scale into the collision weights, as
     // the global-load kernel does
     constexpr bool prescale = TAU1 && std::is_same<S, __half>::value;
-    // every decision to go on is taken by the whole block (__syncthreads_and),
-    // so no thread can leave the loop while others wait at a barrier
+    // Each thread waits for its rows on its own: the slots are written once
+    // and only read afterwards, so warps need no block barrier and run
+    // decoupled.  Thread 0 waits for every row (inactive or not), so that
+    // all copies have landed before the block can release its shared memory.
     bool ok = true;
-    for (int y = yb; y < ye; ++y) {
-        ok = __syncthreads_and(tma_wait(bar + (y - yb), 0u));
-        if (!ok) break;
+    for (int y = yb; y < ye && (active || tid == 0); ++y) {
+        if (!tma_wait(bar + (y - yb), 0u)) {
+            ok = false;
+            break;
+        }
         if (active) {
             const S* sl = stage + (y - yb) * L::slot + c;
             float f[9], h[9];
@@ -198,10 +203,11 @@ __device__ __forceinline__ void staged_block(const KConst<float>& k, const CUten
             store_planes<S, float>(dst + at, k.plane32, fo, ho, prescale ? 1.0f : k.inv_scale, &dither);
         }
     }
-    if (!ok && tid == 0) {
+    if (!ok) {
         atomicOr(k.flag, 2);
         // let this block's copies land before its shared memory is released
-        for (int r = yb; r < ye; ++r) (void)tma_wait(bar + (r - yb), 0u);
+        if (tid == 0)
+            for (int r = yb; r < ye; ++r) (void)tma_wait(bar + (r - yb), 0u);
     }
 }
 
