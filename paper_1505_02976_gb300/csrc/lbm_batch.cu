@@ -65,7 +65,7 @@ struct lbm_batch {
     const lbm::BatchItem* items(int t) const { return (const lbm::BatchItem*)(ws + off_items[t]); }
     int* bounds() const { return (int*)(ws + off_bounds); }
     const CUtensorMap* maps(int buffer) const { return (const CUtensorMap*)(ws + off_maps) + (size_t)buffer * n; }
-    const lbm::BatchItem* sitems() const { return (const lbm::BatchItem*)(ws + off_sitems); }
+    const lbm::StagedItem* sitems() const { return (const lbm::StagedItem*)(ws + off_sitems); }
     size_t es() const { return precision == LBM_F64 ? 8 : 4; }
 };
 
@@ -138,11 +138,11 @@ bool stageable(const std::vector<lbm_params>& prm) {
 
 // Work items of the staged kernel: every cavity's bands of 128 columns x
 // segments of `rows` rows, cavity by cavity.
-std::vector<lbm::BatchItem> make_staged_items(const std::vector<lbm_params>& prm, int rows) {
-    std::vector<lbm::BatchItem> v;
+std::vector<lbm::StagedItem> make_staged_items(const std::vector<lbm_params>& prm, int rows) {
+    std::vector<lbm::StagedItem> v;
     for (int c = 0; c < (int)prm.size(); ++c)
         for (int y0 = 0; y0 < prm[c].ny; y0 += rows)
-            for (int x0 = 0; x0 < prm[c].nx; x0 += 128) v.push_back({c, x0, y0, 2});
+            for (int x0 = 0; x0 < prm[c].nx; x0 += 128) v.push_back({c, x0, y0, prm[c].ny});
     return v;
 }
 
@@ -201,7 +201,7 @@ lbm_status batch_layout(const lbm_params* p, int n, lbm_batch* b, std::string* w
         if (ns >= (size_t)1 << 31) { *why = "batch too large"; return LBM_ERR_ARG; }
         b->n_sitems = (int)ns;
         b->off_maps = o; o += align256((size_t)2 * n * sizeof(CUtensorMap));
-        b->off_sitems = o; o += align256(ns * sizeof(lbm::BatchItem));
+        b->off_sitems = o; o += align256(ns * sizeof(lbm::StagedItem));
     }
     b->off_fields = o; o += align256(4 * b->max_cells * sizeof(double));
     b->off_nu = o; o += align256((size_t)n * sizeof(double));
@@ -400,8 +400,8 @@ lbm_status lbm_batch_create(const lbm_params* p, int32_t n, void* stream, void* 
                                                &b->hmaps[i][c]);
         }
         if (ok) {
-            std::vector<lbm::BatchItem> it = make_staged_items(b->prm, lbm::tma_batch_rows());
-            s = upload(b->off_sitems, it.data(), it.size() * sizeof(lbm::BatchItem), "staged work list");
+            std::vector<lbm::StagedItem> it = make_staged_items(b->prm, lbm::tma_batch_rows());
+            s = upload(b->off_sitems, it.data(), it.size() * sizeof(lbm::StagedItem), "staged work list");
             for (int i = 0; i < 2 && s == LBM_OK; ++i)
                 s = upload(b->off_maps + (size_t)i * n * sizeof(CUtensorMap), b->hmaps[i].data(),
                            (size_t)n * sizeof(CUtensorMap), "tensor maps");

@@ -80,9 +80,7 @@ struct BatchCavity {
 // Work item of the batched step.  kind 0: a tile of tile_x x (128/tile_x)
 // nodes with origin (a, b) -- its interior nodes only; kind 1: the wall
 // nodes a .. a + b - 1 (b <= 128) of the cavity in perimeter order (S row,
-// N row, W column, E column, walled sides only); kind 2 (the staged kernel):
-// the band of 128 columns from x = a and the segment of rows from y = b,
-// wall and interior nodes.
+// N row, W column, E column, walled sides only).
 struct BatchItem {
     int cavity, a, b, kind;
 };
@@ -133,11 +131,17 @@ int tma_rows_default(const KConst<float>& k);
 template <class S>
 cudaError_t launch_step_tma(const KConst<float>& k, const CUtensorMap& tm, const S* src, S* dst, int rows,
                             uint32_t step, cudaStream_t st);
+// Work item of the staged batched step: the band of 128 columns from x0 and
+// the segment of rows from y0 of a cavity ny rows high.
+struct StagedItem {
+    int cavity, x0, y0, ny;
+};
+
 // Staged step of a batch of FP32 cavities walled on all four sides: one
-// block per work item {cavity, x0, y0, kind 2} (bands of 128 columns,
-// segments of tma_batch_rows() rows, sorted by cavity); maps[c] is cavity c's
-// tensor map of the source buffer.
-cudaError_t launch_step_batch_tma(const BatchCavity<float>* cav, const CUtensorMap* maps, const BatchItem* items,
+// block per work item (bands of 128 columns, segments of tma_batch_rows()
+// rows, sorted by cavity); maps[c] is cavity c's tensor map of the source
+// buffer.
+cudaError_t launch_step_batch_tma(const BatchCavity<float>* cav, const CUtensorMap* maps, const StagedItem* items,
                                   int n_items, const float* src, float* dst, uint32_t step, cudaStream_t st);
 int tma_batch_rows();
 // One wait that must give up (nothing arrives): sets bit 1 of *flag.

@@ -125,36 +125,45 @@ __device__ __forceinline__ bool tma_wait(uint64_t* bar, uint32_t parity,
     return false;
 }
 
-// One block of the staged step: columns x0 .. x0 + 127 and rows y0 ..
-// y0 + rows - 1 (rows <= kTRows) of the lattice k, whose population buffers
-// src / dst the tensor map tm describes.  step: the step number (the
-// stochastic rounding of FP16 stores draws from it).  smem_raw: the block's
-// dynamic shared memory (TmaLayout<S>::smem bytes).
-template <class S, bool EPS_FIELD, bool TAU1>
-__device__ __forceinline__ void staged_block(const KConst<float>& k, const CUtensorMap* tm, const S* __restrict__ src,
-                                             S* __restrict__ dst, int x0, int y0, int rows, uint32_t step,
-                                             unsigned char* smem_raw) {
-    using L = TmaLayout<S>;
+// Shared memory of a staged block: the slots (128-byte aligned) and one
+// mbarrier per slot, initialised by thread 0 (the caller synchronises the
+// block before any thread waits on them).
+template <class S>
+__device__ __forceinline__ void staged_setup(unsigned char* smem_raw, S*& stage, uint64_t*& bar) {
     unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-    S* stage = reinterpret_cast<S*>(base);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(base + (size_t)kTRows * L::slot * sizeof(S));
-    const int tid = threadIdx.x;
-    const int y1 = min(y0 + rows, k.ny);
-    const int yb = max(y0, 1), ye = min(y1, k.ny - 1);  // interior rows of the segment (at most kTRows)
-    const int x = x0 + tid;
-    if (tid == 0) {
+    stage = reinterpret_cast<S*>(base);
+    bar = reinterpret_cast<uint64_t*>(base + (size_t)kTRows * TmaLayout<S>::slot * sizeof(S));
+    if (threadIdx.x == 0) {
         for (int s = 0; s < kTRows; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar + s)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
-    // the previous step's writes must be visible before the first load
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    // output row r lands in slot r - yb (each slot and barrier is used once)
-    if (tid == 0)
-        for (int r = yb; r < ye; ++r)
-            tma_load_slot(tm, stage + (r - yb) * L::slot, bar + (r - yb), x0 - L::halo, r);
-    // wall nodes of the segment, in parallel, while those loads fly
+}
+
+// The tensor copies of one block (one thread): output row r of the interior
+// rows yb .. ye - 1 of the segment y0 .. y0 + rows - 1 lands in slot r - yb
+// (each slot and barrier is used once).
+template <class S>
+__device__ __forceinline__ void staged_issue(const CUtensorMap* tm, S* stage, uint64_t* bar, int x0, int y0, int rows,
+                                             int ny) {
+    const int yb = max(y0, 1), ye = min(min(y0 + rows, ny), ny - 1);
+    for (int r = yb; r < ye; ++r)
+        tma_load_slot(tm, stage + (r - yb) * TmaLayout<S>::slot, bar + (r - yb), x0 - TmaLayout<S>::halo, r);
+}
+
+// One block of the staged step once its copies are issued and its barriers
+// are visible: columns x0 .. x0 + 127 and rows y0 .. y0 + rows - 1 (rows <=
+// kTRows) of the lattice k with population buffers src / dst.  step: the
+// step number (the stochastic rounding of FP16 stores draws from it).
+template <class S, bool EPS_FIELD, bool TAU1>
+__device__ __forceinline__ void staged_rows(const KConst<float>& k, const S* __restrict__ src, S* __restrict__ dst,
+                                            int x0, int y0, int rows, uint32_t step, const S* stage, uint64_t* bar) {
+    using L = TmaLayout<S>;
+    const int tid = threadIdx.x;
+    const int y1 = min(y0 + rows, k.ny);
+    const int yb = max(y0, 1), ye = min(y1, k.ny - 1);  // interior rows of the segment (at most kTRows)
+    const int x = x0 + tid;
+    // wall nodes of the segment, in parallel, while the copies fly
     if (x < k.nx) {
         if (y0 == 0) wall_update(k, src, dst, x, 0, step);
         if (y1 == k.ny) wall_update(k, src, dst, x, k.ny - 1, step);
@@ -211,43 +220,61 @@ __device__ __forceinline__ void staged_block(const KConst<float>& k, const CUten
     }
 }
 
-// The staged step of one lattice: block (bx, by) owns band bx and rows
-// by * rows .. by * rows + rows - 1.
+// The staged step of one lattice: block (bx, by) owns band bx and a segment
+// of `rows` rows.  The two segments holding the S and N wall rows (a full row
+// of out-of-line wall updates each) are taken by the first two block rows,
+// so that the blocks the hardware starts last are plain interior ones.
 template <class S, bool EPS_FIELD, bool TAU1>
 __global__ void __launch_bounds__(kTBand, TmaLayout<S>::blocks)
 k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUtensorMap tm,
            const S* __restrict__ src, S* __restrict__ dst, int rows, uint32_t step) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    staged_block<S, EPS_FIELD, TAU1>(k, &tm, src, dst, blockIdx.x * kTBand, blockIdx.y * rows, rows, step,
-                                     smem_raw);
+    S* stage;
+    uint64_t* bar;
+    staged_setup<S>(smem_raw, stage, bar);
+    const int by = (int)blockIdx.y, nseg = (int)gridDim.y;
+    const int seg = by == 0 ? 0 : (by == 1 ? nseg - 1 : by - 1);
+    const int x0 = blockIdx.x * kTBand, y0 = seg * rows;
+    __syncthreads();  // barriers initialised (the other threads go on while thread 0 issues)
+    // the previous step's writes must be visible before the first copy
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (threadIdx.x == 0) staged_issue<S>(&tm, stage, bar, x0, y0, rows, k.ny);
+    staged_rows<S, EPS_FIELD, TAU1>(k, src, dst, x0, y0, rows, step, stage, bar);
 }
 
 // The staged step of a batch of FP32 cavities walled on all four sides: block
-// i takes work item i = (cavity, band origin x0, segment origin y0) of a list
-// sorted by cavity; the cavity's constants are staged in shared memory and
-// its tensor map (for the source buffer) is read from global memory.
+// i takes work item i = (cavity, band origin x0, segment origin y0, cavity
+// height) of a list sorted by cavity.  Thread 0 issues the block's copies
+// (the cavity's tensor map for the source buffer is read from global
+// memory) as soon as the previous step has finished, while the block copies
+// the cavity's constants into shared memory.
 __global__ void __launch_bounds__(kTBand, TmaLayout<float>::blocks)
 k_step_batch_tma(const BatchCavity<float>* __restrict__ cav, const CUtensorMap* __restrict__ maps,
-                 const BatchItem* __restrict__ items, const float* __restrict__ src, float* __restrict__ dst,
+                 const StagedItem* __restrict__ items, const float* __restrict__ src, float* __restrict__ dst,
                  uint32_t step) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ KConst<float> ks;
     __shared__ long long off;
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const StagedItem w = items[blockIdx.x];
+    float* stage;
+    uint64_t* bar;
+    staged_setup<float>(smem_raw, stage, bar);
     // the descriptors and maps are written once, before any step: they may be
     // read before the previous step has finished
-    const BatchItem w = items[blockIdx.x];
     const int* from = reinterpret_cast<const int*>(&cav[w.cavity].k);
     int* to = reinterpret_cast<int*>(&ks);
     for (int q = threadIdx.x; q < (int)(sizeof(KConst<float>) / sizeof(int)); q += kTBand) to[q] = from[q];
     if (threadIdx.x == 0) off = cav[w.cavity].offset;
-    __syncthreads();
-    const CUtensorMap* tm = maps + w.cavity;
+    // the previous step's writes must be visible before the copies
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (threadIdx.x == 0) staged_issue<float>(maps + w.cavity, stage, bar, w.x0, w.y0, kTRows, w.ny);
+    __syncthreads();  // constants, offset and barriers
     if (ks.omf == 0.f && ks.omT == 0.f)
-        staged_block<float, false, true>(ks, tm, src + off, dst + off, w.a, w.b, kTRows, step, smem_raw);
+        staged_rows<float, false, true>(ks, src + off, dst + off, w.x0, w.y0, kTRows, step, stage, bar);
     else
-        staged_block<float, false, false>(ks, tm, src + off, dst + off, w.a, w.b, kTRows, step, smem_raw);
+        staged_rows<float, false, false>(ks, src + off, dst + off, w.x0, w.y0, kTRows, step, stage, bar);
 }
 
 // Self-test of the bounded wait: an mbarrier that nothing arrives on, waited
@@ -353,7 +380,7 @@ cudaError_t launch_step_tma(const KConst<float>& k, const CUtensorMap& tm, const
                 : launch_tma<S, false, false>(cfg, k, tm, src, dst, rows, step);
 }
 
-cudaError_t launch_step_batch_tma(const BatchCavity<float>* cav, const CUtensorMap* maps, const BatchItem* items,
+cudaError_t launch_step_batch_tma(const BatchCavity<float>* cav, const CUtensorMap* maps, const StagedItem* items,
                                   int n_items, const float* src, float* dst, uint32_t step, cudaStream_t st) {
     if (n_items < 1) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
