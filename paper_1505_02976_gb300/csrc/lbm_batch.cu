@@ -137,13 +137,19 @@ bool stageable(const std::vector<lbm_params>& prm) {
 }
 
 // Work items of the staged kernel: every cavity's bands of 128 columns x
-// segments of `rows` rows, cavity by cavity.
+// segments of `rows` rows, cavity by cavity.  The segments holding a cavity's
+// S or N wall row (a full row of out-of-line wall updates) come first, so
+// that the blocks the hardware starts last are plain interior ones.
+// Segments do not share source rows, so the order costs no extra traffic.
 std::vector<lbm::StagedItem> make_staged_items(const std::vector<lbm_params>& prm, int rows) {
-    std::vector<lbm::StagedItem> v;
+    std::vector<lbm::StagedItem> walls, inner;
     for (int c = 0; c < (int)prm.size(); ++c)
-        for (int y0 = 0; y0 < prm[c].ny; y0 += rows)
+        for (int y0 = 0; y0 < prm[c].ny; y0 += rows) {
+            std::vector<lbm::StagedItem>& v = (y0 == 0 || y0 + rows >= prm[c].ny) ? walls : inner;
             for (int x0 = 0; x0 < prm[c].nx; x0 += 128) v.push_back({c, x0, y0, prm[c].ny});
-    return v;
+        }
+    walls.insert(walls.end(), inner.begin(), inner.end());
+    return walls;
 }
 
 // Block ranges of equal estimated cost: bounds[k] is the first item of block k.

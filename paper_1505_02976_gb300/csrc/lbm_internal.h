@@ -139,8 +139,8 @@ struct StagedItem {
 
 // Staged step of a batch of FP32 cavities walled on all four sides: one
 // block per work item (bands of 128 columns, segments of tma_batch_rows()
-// rows, sorted by cavity); maps[c] is cavity c's tensor map of the source
-// buffer.
+// rows; the segments holding wall rows first, each group cavity by cavity);
+// maps[c] is cavity c's tensor map of the source buffer.
 cudaError_t launch_step_batch_tma(const BatchCavity<float>* cav, const CUtensorMap* maps, const StagedItem* items,
                                   int n_items, const float* src, float* dst, uint32_t step, cudaStream_t st);
 int tma_batch_rows();

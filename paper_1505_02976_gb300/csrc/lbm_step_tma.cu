@@ -245,7 +245,7 @@ k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUte
 
 // The staged step of a batch of FP32 cavities walled on all four sides: block
 // i takes work item i = (cavity, band origin x0, segment origin y0, cavity
-// height) of a list sorted by cavity.  Thread 0 issues the block's copies
+// height) of the work list.  Thread 0 issues the block's copies
 // (the cavity's tensor map for the source buffer is read from global
 // memory) as soon as the previous step has finished, while the block copies
 // the cavity's constants into shared memory.
