@@ -6,28 +6,27 @@
 // pulled values of every interior node reach the block through shared
 // memory.  Pull streaming reads plane i of output row y from global row
 // y - c_iy, so each plane of each global row is used by exactly one output
-// row: a slot holds the 17 planes one output row needs, each plane
-// loaded (one 3-D tensor copy of 128 + 2 halo columns x 1 row x 1 plane)
-// from its own source row.  A block owns a band of 128 columns and a segment of up to
-// kTRows rows; one thread issues all of the block's copies (17 plane rows
-// per output row, 37 KB for 4 FP32 rows) at its start, and each thread waits
-// on each row's mbarrier instead of on its own global loads (no block
-// barrier between rows: the slots are written once).  Many short
-// blocks keep the SMs busy to the end of the step (measured on the 2048^2
-// and 8192^2 FP32 cavities: 4-row segments beat 2, 3, 5, 6, 8, 16, 32 and
-// 64 rows streamed through a ring of 2 to 6 row slots, and the global-load
-// step).
+// row: a slot holds the 17 planes one output row needs, each plane loaded by
+// one 3-D tensor copy (128 + 2 halo columns x 1 row x 1 plane) from its own
+// source row.  A block owns a band of 128 columns and a segment of up to
+// kTRows rows.  One thread issues all of the block's copies at its start (17
+// plane rows per output row, 37 KB for 4 FP32 rows), and each thread waits
+// on each row's mbarrier instead of on its own global loads; the slots are
+// written once, so no block barrier separates the rows.  Many short blocks
+// keep the SMs busy to the end of the step: on the 2048^2 and 8192^2 FP32
+// cavities, 4-row segments beat 2, 3, 5, 6, 8, 16, 32 and 64 rows streamed
+// through a ring of 2 to 6 row slots, and the global-load step.
 //
 // Wall nodes (the segment's part of the W and E columns, and the S and N
-// rows) are updated before the row loop, all in parallel, while the first
-// rows' loads are in flight; the row loop then runs interior nodes only.
+// rows) are updated before the row loop, all in parallel, while the copies
+// are in flight; the row loop then runs interior nodes only.
 //
-// Used for FP32 and FP16 storage on lattices walled on all four sides (a periodic
-// side would need wrapped halo columns, which the tile load does not give):
-// every interior node pulls only from nodes inside the lattice, and the
-// zero fill of out-of-range boxes is never read.  Waits are bounded: a wait
-// that gives up sets bit 1 of the handle's flag (LBM_ERR_TIMEOUT) and the
-// block stops after its copies in flight have landed.
+// Used for FP32 and FP16 storage on lattices walled on all four sides (a
+// periodic side would need wrapped halo columns, which the tile copy does not
+// give): every interior node pulls only from nodes inside the lattice, and
+// the zero fill of out-of-range boxes is never read.  Waits are bounded: a
+// wait that gives up sets bit 1 of the handle's flag (LBM_ERR_TIMEOUT) and
+// the block stops after its copies in flight have landed.
 #include <cuda.h>
 #include <math.h>
 
