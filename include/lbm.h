@@ -131,7 +131,7 @@ lbm_status lbm_set_moment_segments(lbm_handle* h, int32_t segments);
  * staged = 0 selects the kernel in which every thread loads its own 17
  * values from global memory; staged = 1 restores the staged kernel
  * (LBM_ERR_ARG where it is unavailable: FP64, a periodic side, the moment
- * state, a lattice under 4 x 4, or a driver without tensor-map encoding).
+ * state, a lattice under 4 x 4, or a CUDA driver without tensor-map encoding).
  * Both kernels run the same per-node arithmetic (results agree to rounding;
  * bit for bit at tau_f = tau_T = 1).  lbm_step_staged returns 1 when the
  * next step uses staged rows, else 0. */

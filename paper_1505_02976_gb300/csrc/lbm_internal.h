@@ -121,7 +121,7 @@ int moment_segments_default(const KConst<R>& k);
 
 // ------------------------------------------- step with TMA-staged rows
 // Lattices walled on all four sides, FP32 or FP16 storage (S): the tensor
-// map of a population buffer (false if the driver's encoder is unavailable
+// map of a population buffer (false if the CUDA driver's encoder is unavailable
 // or rejects it), the default rows per block segment, and the launch (step
 // numbers the FP16 stochastic rounding).
 bool tma_step_supported(const KConst<float>& k);
