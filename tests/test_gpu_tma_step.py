@@ -21,9 +21,9 @@ pytestmark = pytest.mark.gpu
 SIZES = [(300, 250), (129, 517), (4, 4), (131, 5), (517, 9)]
 
 
-def _run(p, precision, fields, steps, staged):
+def _run(p, precision, fields, steps, staged, eps_field=None):
     g = lbm.Lattice(p, precision)
-    g.set_fields(*fields)
+    g.set_fields(*fields, eps_field=eps_field)
     if not staged:
         g.staged = False
     assert g.staged == staged
@@ -55,6 +55,19 @@ def test_staged_step_matches_global_loads(precision, nx, ny):
         for k in ("ux", "uy", "T", "p"):
             assert np.array_equal(ma[k], mb[k]), k
         bt.close()
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_staged_step_with_porosity_field_matches_global_loads(precision):
+    """Porosity field (per-node constants from K(eps), F_eps(eps)) on a
+    260 x 133 cavity: staged and global-load kernels give the same bits."""
+    p = W.cavity(260, 1e5, 1e-3, 0.5, ny=133)
+    eps = W.gaussian_random_field(260, corr=8.0, seed=9)[:133, :]
+    fields = W.random_fields(p, seed=4, amp_u=2e-3, amp_T=0.3)
+    fa, ga = _run(p, precision, fields, 40, True, eps_field=eps).get_state()
+    fb, gb = _run(p, precision, fields, 40, False, eps_field=eps).get_state()
+    assert np.array_equal(fa[1:], fb[1:]) and np.array_equal(ga, gb)
+    assert np.all(np.isfinite(ga))
 
 
 def test_staging_switch_is_refused_where_unavailable():
