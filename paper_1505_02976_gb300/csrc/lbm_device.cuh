@@ -651,7 +651,8 @@ __device__ __forceinline__ FastState<R> fast_moments(const KConst<R>& k, const R
     s.uy = vy * iden;
     if (!isfinite(s.th + s.ux + s.uy)) atomicOr(k.flag, 1);
     s.uu = s.ux * s.ux + s.uy * s.uy;
-    const R drag = k.e_nuK + k.e_FK * sqrt(s.uu);
+    // |u| = |v| / (c0 + sqrt(c0^2 + c1 |v|)): no second square root
+    const R drag = k.e_nuK + k.e_FK * (vmag * iden);
     s.Fx = k.eps * k.ax - drag * s.ux;
     s.Fy = k.eps * Gy - drag * s.uy;
     s.uF = s.ux * s.Fx + s.uy * s.Fy;
@@ -668,8 +669,11 @@ __device__ __forceinline__ FastState<R> fast_moments(const KConst<R>& k, const R
     const R Nx = hx + s.T * (R(0.5) * s.Fx - s.ux) + qs * s.ux;
     const R Ny = hy + s.T * (R(0.5) * s.Fy - s.uy) + qs * s.uy;
     const R a = k.a_const - R(0.5) * s.ep * k.inv_rho0;
-    const R ia = R(1) / a;
-    const R t = k.bcoef * (s.ux * Nx + s.uy * Ny) / (a - k.bcoef * s.uu);
+    const R d = a - k.bcoef * s.uu;
+    // one reciprocal for 1/a = d r and 1/d = a r, r = 1/(a d)
+    const R r = R(1) / (a * d);
+    const R t = k.bcoef * (s.ux * Nx + s.uy * Ny) * (a * r);
+    const R ia = d * r;
     s.gx = (Nx + t * s.ux) * ia;
     s.gy = (Ny + t * s.uy) * ia;
     return s;
