@@ -56,7 +56,8 @@ typedef enum {
     LBM_ERR_NONFINITE = -3,    /* a NaN/Inf appeared in u or T during a step */
     LBM_ERR_TIMEOUT = -4,      /* a bounded device-side wait gave up */
     LBM_ERR_PARAM_RANGE = -5,  /* parameters outside the model's range (Sec. 4) */
-    LBM_ERR_OOM = -6           /* workspace too small or allocation failed */
+    LBM_ERR_OOM = -6,          /* workspace too small or allocation failed */
+    LBM_ERR_GUARD = -7         /* a guard word of the workspace was overwritten */
 } lbm_status;
 
 /* Storage type of the populations.  LBM_F64 computes in FP64, LBM_F32 in
@@ -213,6 +214,14 @@ lbm_status lbm_step(lbm_handle* h, int64_t n);
  * LBM_ERR_NONFINITE if any step since the last reset produced a non-finite
  * velocity or temperature. */
 lbm_status lbm_sync(lbm_handle* h);
+
+/* Out-of-bounds detection (the paper has no counterpart): every region of
+ * the handle's workspace (population or moment buffers, fields, snapshot,
+ * scratch) is followed by 256 guard bytes of 0xA5, written by lbm_create.
+ * Synchronises the stream and compares them; LBM_ERR_GUARD names the first
+ * overwritten guard (a kernel wrote past the end of the region before it).
+ * The workspace size reported by lbm_workspace_size includes the guards. */
+lbm_status lbm_check_guards(lbm_handle* h);
 
 /* Failure-detection self-test (the paper has no counterpart): launches, on
  * the handle's stream, one kernel whose bounded device-side wait cannot
@@ -393,6 +402,10 @@ int64_t lbm_batch_steps_done(const lbm_batch* b);
 
 /* Kernel launches issued for steps (a graph replay counts its 50 launches). */
 int64_t lbm_batch_kernel_launches(const lbm_batch* b);
+
+/* As lbm_check_guards, for the batch workspace (both population buffers,
+ * descriptors, work lists, tensor maps, fields and scratch). */
+lbm_status lbm_batch_check_guards(lbm_batch* b);
 
 #ifdef __cplusplus
 }

@@ -431,6 +431,7 @@ lbm_status run_adjoint(lbm_handle* h, const lbm::KConst<R>& k, int64_t n, int64_
 
 extern "C" lbm_status lbm_adjoint(lbm_handle* h, int64_t n_steps, int64_t segment, int side, double* loss,
                                   double* dloss_deps, double* dloss_dTbc) {
+    const lbm_host::NvtxRange range("lbm_adjoint");
     if (!h) return LBM_ERR_ARG;
     if (n_steps < 1 || segment < 0 || side < 0 || side > 3 || !loss)
         return lbm_handle_fail(h, LBM_ERR_ARG, "bad step count, segment, side or null loss");

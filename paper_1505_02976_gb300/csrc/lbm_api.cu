@@ -200,13 +200,33 @@ lbm_status lbm_create(const lbm_params* p, void* stream, void* workspace, size_t
     h->diag.L = d.L;
     h->diag.dT = d.dT;
     for (int q = 0; q < 4; ++q) h->diag.T_bc[q] = p->T_bc[q];
-    s = lbm_set_fields(h, nullptr, nullptr, nullptr, nullptr, 1);
+    s = LBM_OK;
+    for (int g = 0; g < L.n_guards && s == LBM_OK; ++g) {
+        const cudaError_t e = cudaMemsetAsync(h->ws + L.guard[g], kGuardByte, kGuardBytes, h->stream);
+        if (e != cudaSuccess) s = cuda_fail(h, e, "guard words");
+    }
+    if (s == LBM_OK) s = lbm_set_fields(h, nullptr, nullptr, nullptr, nullptr, 1);
     if (s != LBM_OK) {
         g_create_error = h->err;
         lbm_destroy(h);
         return s;
     }
     *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_check_guards(lbm_handle* h) {
+    if (!h) return LBM_ERR_ARG;
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "stream synchronise");
+    unsigned char w[kGuardBytes];
+    for (int g = 0; g < h->L.n_guards; ++g) {
+        LBM_CUDA(h, cudaMemcpy(w, h->ws + h->L.guard[g], kGuardBytes, cudaMemcpyDeviceToHost), "guard read");
+        for (size_t b = 0; b < kGuardBytes; ++b)
+            if (w[b] != kGuardByte)
+                return fail(h, LBM_ERR_GUARD,
+                            "guard word after workspace region " + std::to_string(g) + " overwritten at byte " +
+                                std::to_string(b));
+    }
     return LBM_OK;
 }
 
@@ -225,6 +245,7 @@ const char* lbm_last_error(const lbm_handle* h) {
 
 lbm_status lbm_set_fields(lbm_handle* h, const double* T, const double* ux, const double* uy,
                           const double* eps_field, int on_device) {
+    const NvtxRange range("lbm_set_fields");
     if (!h) return LBM_ERR_ARG;
     double* F = h->fields();
     const size_t N = h->N();
@@ -281,6 +302,7 @@ lbm_status lbm_set_fields(lbm_handle* h, const double* T, const double* ux, cons
 }
 
 lbm_status lbm_step(lbm_handle* h, int64_t n) {
+    const NvtxRange range("lbm_step");
     if (!h || n < 0) return h ? fail(h, LBM_ERR_ARG, "negative step count") : LBM_ERR_ARG;
     if (h->timeout) return fail(h, LBM_ERR_TIMEOUT, "a bounded wait of the TMA step gave up");
     if (h->nonfinite) return fail(h, LBM_ERR_NONFINITE, "non-finite velocity or temperature");
@@ -369,6 +391,7 @@ lbm_status lbm_wait_selftest(lbm_handle* h) {
 }
 
 lbm_status lbm_moments(lbm_handle* h, double* p, double* ux, double* uy, double* T, int on_device) {
+    const NvtxRange range("lbm_moments");
     if (!h) return LBM_ERR_ARG;
     LBM_POPS(h);
     double* F = h->fields();
@@ -413,6 +436,7 @@ lbm_status lbm_stream_function(lbm_handle* h, double* psi, int on_device, double
 }
 
 lbm_status lbm_nusselt(lbm_handle* h, int side, double* nu_mean, double* nu_local) {
+    const NvtxRange range("lbm_nusselt");
     if (!h) return LBM_ERR_ARG;
     if (side < 0 || side > 3 || !nu_mean) return fail(h, LBM_ERR_ARG, "bad side or null output");
     const int n = side <= 1 ? h->prm.ny : h->prm.nx;
@@ -433,6 +457,7 @@ lbm_status lbm_nusselt(lbm_handle* h, int side, double* nu_mean, double* nu_loca
 }
 
 lbm_status lbm_residual(lbm_handle* h, double* res_u, double* res_T) {
+    const NvtxRange range("lbm_residual");
     if (!h || !res_u || !res_T) return h ? fail(h, LBM_ERR_ARG, "null output") : LBM_ERR_ARG;
     lbm_status s = reset_snapshot(h);
     if (s != LBM_OK) return s;
@@ -586,6 +611,7 @@ struct CkptHeader {
 extern "C" {
 
 lbm_status lbm_checkpoint(lbm_handle* h, const char* path, int save) {
+    const NvtxRange range("lbm_checkpoint");
     if (!h || !path) return h ? fail(h, LBM_ERR_ARG, "null path") : LBM_ERR_ARG;
     const size_t es = elem_size(h->prm.precision);
     const bool mk = h->moments_kind();

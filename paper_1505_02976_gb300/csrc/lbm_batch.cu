@@ -52,6 +52,7 @@ struct lbm_batch {
     // maps of every cavity in both buffers (device: maps[buffer * n + c])
     bool staged, staged_ready;
     size_t off_maps, off_sitems;
+    std::vector<size_t> guards;        // offsets of the guard words after each region
     int n_sitems;
     std::vector<CUtensorMap> hmaps[2];
     cudaGraphExec_t graph[2];          // captured kGraphChunk steps, one per starting buffer
@@ -191,27 +192,35 @@ lbm_status batch_layout(const lbm_params* p, int n, lbm_batch* b, std::string* w
     if (elems >= (size_t)1 << 40) { *why = "batch too large"; return LBM_ERR_ARG; }
     b->buf_elems = elems;
     size_t o = 0;
-    b->off_buf[0] = o; o += align256(elems * es);
-    b->off_buf[1] = o; o += align256(elems * es);
-    b->off_cav = o; o += align256((size_t)n * (prec == LBM_F64 ? sizeof(lbm::BatchCavity<double>) : sizeof(lbm::BatchCavity<float>)));
+    b->guards.clear();
+    // each region is followed by a guard word (see lbm_batch_check_guards)
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += align256(bytes);
+        b->guards.push_back(o);
+        o += kGuardBytes;
+        return at;
+    };
+    b->off_buf[0] = take(elems * es);
+    b->off_buf[1] = take(elems * es);
+    b->off_cav = take((size_t)n * (prec == LBM_F64 ? sizeof(lbm::BatchCavity<double>) : sizeof(lbm::BatchCavity<float>)));
     for (int t = 0; t < 3; ++t) {
         b->n_items[t] = (int)make_items(b->prm, kTiles[t], &b->cum[t]).size();
-        b->off_items[t] = o;
-        o += align256((size_t)b->n_items[t] * sizeof(lbm::BatchItem));
+        b->off_items[t] = take((size_t)b->n_items[t] * sizeof(lbm::BatchItem));
     }
-    b->off_bounds = o; o += align256((size_t)(kMaxGrid + 1) * sizeof(int));
+    b->off_bounds = take((size_t)(kMaxGrid + 1) * sizeof(int));
     b->n_sitems = 0;
     b->off_maps = b->off_sitems = o;
     if (stageable(b->prm)) {
         const size_t ns = make_staged_items(b->prm, lbm::tma_batch_rows()).size();
         if (ns >= (size_t)1 << 31) { *why = "batch too large"; return LBM_ERR_ARG; }
         b->n_sitems = (int)ns;
-        b->off_maps = o; o += align256((size_t)2 * n * sizeof(CUtensorMap));
-        b->off_sitems = o; o += align256(ns * sizeof(lbm::StagedItem));
+        b->off_maps = take((size_t)2 * n * sizeof(CUtensorMap));
+        b->off_sitems = take(ns * sizeof(lbm::StagedItem));
     }
-    b->off_fields = o; o += align256(4 * b->max_cells * sizeof(double));
-    b->off_nu = o; o += align256((size_t)n * sizeof(double));
-    b->off_flag = o; o += 256;
+    b->off_fields = take(4 * b->max_cells * sizeof(double));
+    b->off_nu = take((size_t)n * sizeof(double));
+    b->off_flag = take(256);
     b->ws_bytes = o;
     return LBM_OK;
 }
@@ -390,8 +399,14 @@ lbm_status lbm_batch_create(const lbm_params* p, int32_t n, void* stream, void* 
         if (e != cudaSuccess) return bcuda(b, e, what);
         return LBM_OK;
     };
-    if (b->precision == LBM_F64) s = upload(b->off_cav, b->cav64.data(), n * sizeof(lbm::BatchCavity<double>), "descriptors");
-    else s = upload(b->off_cav, b->cav32.data(), n * sizeof(lbm::BatchCavity<float>), "descriptors");
+    for (size_t g = 0; g < b->guards.size() && s == LBM_OK; ++g) {
+        const cudaError_t e = cudaMemsetAsync(b->ws + b->guards[g], kGuardByte, kGuardBytes, b->stream);
+        if (e != cudaSuccess) s = bcuda(b, e, "guard words");
+    }
+    if (s == LBM_OK)
+        s = b->precision == LBM_F64
+                ? upload(b->off_cav, b->cav64.data(), n * sizeof(lbm::BatchCavity<double>), "descriptors")
+                : upload(b->off_cav, b->cav32.data(), n * sizeof(lbm::BatchCavity<float>), "descriptors");
     for (int t = 0; t < 3 && s == LBM_OK; ++t) {
         std::vector<lbm::BatchItem> it = make_items(b->prm, kTiles[t], nullptr);
         s = upload(b->off_items[t], it.data(), it.size() * sizeof(lbm::BatchItem), "work list");
@@ -480,6 +495,7 @@ lbm_status lbm_batch_set_fields(lbm_batch* b, int32_t cavity, const double* T, c
 }
 
 lbm_status lbm_batch_step(lbm_batch* b, int64_t n, int mode) {
+    const NvtxRange range("lbm_batch_step");
     if (!b || n < 0) return b ? bfail(b, LBM_ERR_ARG, "negative step count") : LBM_ERR_ARG;
     if (b->timeout) return bfail(b, LBM_ERR_TIMEOUT, "a bounded wait of the staged step gave up");
     if (b->nonfinite) return bfail(b, LBM_ERR_NONFINITE, "non-finite velocity or temperature");
@@ -591,6 +607,21 @@ lbm_status lbm_batch_set_staging(lbm_batch* b, int32_t staged) {
 }
 
 int32_t lbm_batch_staged(const lbm_batch* b) { return b && b->staged ? 1 : 0; }
+
+lbm_status lbm_batch_check_guards(lbm_batch* b) {
+    if (!b) return LBM_ERR_ARG;
+    LBM_BCUDA(b, cudaStreamSynchronize(b->stream), "stream synchronise");
+    unsigned char w[kGuardBytes];
+    for (size_t g = 0; g < b->guards.size(); ++g) {
+        LBM_BCUDA(b, cudaMemcpy(w, b->ws + b->guards[g], kGuardBytes, cudaMemcpyDeviceToHost), "guard read");
+        for (size_t i = 0; i < kGuardBytes; ++i)
+            if (w[i] != kGuardByte)
+                return bfail(b, LBM_ERR_GUARD,
+                             "guard word after workspace region " + std::to_string(g) + " overwritten at byte " +
+                                 std::to_string(i));
+    }
+    return LBM_OK;
+}
 
 lbm_status lbm_batch_nusselt(lbm_batch* b, int side, double* nu_mean) {
     if (!b || side < 0 || side > 3 || !nu_mean) return b ? bfail(b, LBM_ERR_ARG, "bad side or null output") : LBM_ERR_ARG;

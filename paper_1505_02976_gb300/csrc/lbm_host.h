@@ -8,6 +8,8 @@
 
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
 
@@ -95,11 +97,29 @@ inline size_t elem_size(int precision) {
 
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
+// NVTX range over one entry point (visible to Nsight tools; a no-op
+// otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Guard words: kGuardBytes of kGuardByte after every region of a workspace,
+// written at creation and compared on request (lbm_check_guards), so that a
+// kernel writing past the end of any region is detected.
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+constexpr int kMaxGuards = 32;
+
 struct Layout {
     int pitch;
     size_t plane_elems, buf_bytes;
     size_t off_buf[2], off_fields, off_snap, off_nu, off_partial, off_eps, off_ay, off_out, off_flag, total;
     size_t off_mom[2], mom_bytes;  // moment state: two 9-plane buffers; off_buf[0] = off_buf[1] = expansion
+    size_t guard[kMaxGuards];      // offsets of the guard words
+    int n_guards;
 };
 
 inline Layout layout(const lbm_params* p) {
@@ -111,25 +131,34 @@ inline Layout layout(const lbm_params* p) {
     L.buf_bytes = align256(L.plane_elems * es * lbm::NPLANES);
     const size_t N = (size_t)p->nx * p->ny;
     size_t o = 0;
-    L.off_buf[0] = o; o += L.buf_bytes;
+    L.n_guards = 0;
+    // each region is followed by a guard word
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += align256(bytes);
+        L.guard[L.n_guards++] = o;
+        o += kGuardBytes;
+        return at;
+    };
+    L.off_buf[0] = take(L.buf_bytes);
     if (p->moment_state) {
         L.off_buf[1] = L.off_buf[0];
         L.mom_bytes = align256(L.plane_elems * es * lbm::kMPlanes);
-        L.off_mom[0] = o; o += L.mom_bytes;
-        L.off_mom[1] = o; o += L.mom_bytes;
+        L.off_mom[0] = take(L.mom_bytes);
+        L.off_mom[1] = take(L.mom_bytes);
     } else {
-        L.off_buf[1] = o; o += L.buf_bytes;
+        L.off_buf[1] = take(L.buf_bytes);
         L.mom_bytes = 0;
         L.off_mom[0] = L.off_mom[1] = 0;
     }
-    L.off_fields = o; o += align256(4 * N * sizeof(double));
-    L.off_snap = o; o += align256(3 * N * sizeof(double));
-    L.off_nu = o; o += align256((size_t)(p->nx > p->ny ? p->nx : p->ny) * sizeof(double));
-    L.off_partial = o; o += align256((size_t)lbm::residual_blocks(p->nx, p->ny) * 4 * sizeof(double));
-    L.off_eps = o; o += align256(N * sizeof(double));
-    L.off_ay = o; o += align256((size_t)p->ny * sizeof(double));
-    L.off_out = o; o += 256;
-    L.off_flag = o; o += 256;
+    L.off_fields = take(4 * N * sizeof(double));
+    L.off_snap = take(3 * N * sizeof(double));
+    L.off_nu = take((size_t)(p->nx > p->ny ? p->nx : p->ny) * sizeof(double));
+    L.off_partial = take((size_t)lbm::residual_blocks(p->nx, p->ny) * 4 * sizeof(double));
+    L.off_eps = take(N * sizeof(double));
+    L.off_ay = take((size_t)p->ny * sizeof(double));
+    L.off_out = take(256);
+    L.off_flag = take(256);
     L.total = o;
     return L;
 }

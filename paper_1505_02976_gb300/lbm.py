@@ -18,7 +18,7 @@ from . import build as _build
 
 LBM_OK = 0
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NONFINITE",
-          -4: "LBM_ERR_TIMEOUT", -5: "LBM_ERR_PARAM_RANGE", -6: "LBM_ERR_OOM"}
+          -4: "LBM_ERR_TIMEOUT", -5: "LBM_ERR_PARAM_RANGE", -6: "LBM_ERR_OOM", -7: "LBM_ERR_GUARD"}
 PRECISION = {"f64": 0, "f32": 1, "f16": 2}
 BC = {"periodic": 0, "dirichlet": 1, "adiabatic": 2}
 SIDE = {"W": 0, "E": 1, "S": 2, "N": 3}
@@ -32,7 +32,8 @@ EXPORTED = ("lbm_params_default", "lbm_derived", "lbm_workspace_size", "lbm_crea
             "lbm_batch_moments", "lbm_batch_steps_done", "lbm_batch_kernel_launches",
             "lbm_adjoint", "lbm_totals", "lbm_checkpoint", "lbm_set_force_profile",
             "lbm_stream_function", "lbm_set_moment_segments", "lbm_wait_selftest",
-            "lbm_set_step_staging", "lbm_step_staged", "lbm_batch_set_staging", "lbm_batch_staged")
+            "lbm_set_step_staging", "lbm_step_staged", "lbm_batch_set_staging", "lbm_batch_staged",
+            "lbm_check_guards", "lbm_batch_check_guards")
 BATCH_MODE = {"fused": 0, "graph": 1, "per_case": 2}
 
 
@@ -88,6 +89,7 @@ def load(build_if_missing: bool = True):
     L.lbm_step.argtypes = [H, C.c_int64]
     L.lbm_sync.argtypes = [H]
     L.lbm_wait_selftest.argtypes = [H]
+    L.lbm_check_guards.argtypes = [H]
     L.lbm_set_step_staging.argtypes = [H, C.c_int32]
     L.lbm_step_staged.argtypes = [H]
     L.lbm_step_staged.restype = C.c_int32
@@ -110,6 +112,7 @@ def load(build_if_missing: bool = True):
     L.lbm_batch_set_staging.argtypes = [B, C.c_int32]
     L.lbm_batch_staged.argtypes = [B]
     L.lbm_batch_staged.restype = C.c_int32
+    L.lbm_batch_check_guards.argtypes = [B]
     L.lbm_batch_workspace_size.argtypes = [P, C.c_int32, C.POINTER(C.c_size_t)]
     L.lbm_batch_create.argtypes = [P, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(B)]
     L.lbm_batch_destroy.argtypes = [B]
@@ -276,6 +279,11 @@ class Lattice:
     def staged(self, on: bool):
         _check(self.lib.lbm_set_step_staging(self.h, int(bool(on))), self.h)
 
+    def check_guards(self):
+        """Raise LbmError (LBM_ERR_GUARD) if a kernel wrote past the end of
+        any workspace region."""
+        _check(self.lib.lbm_check_guards(self.h), self.h)
+
     def wait_selftest(self):
         """Launch the failure-detection self-test: a bounded device-side
         wait that must give up; the next sync raises LBM_ERR_TIMEOUT."""
@@ -430,6 +438,11 @@ class Batch:
 
     def sync(self):
         self._check(self.lib.lbm_batch_sync(self.h))
+
+    def check_guards(self):
+        """Raise LbmError (LBM_ERR_GUARD) if a kernel wrote past the end of
+        any workspace region."""
+        self._check(self.lib.lbm_batch_check_guards(self.h))
 
     @property
     def staged(self) -> bool:
