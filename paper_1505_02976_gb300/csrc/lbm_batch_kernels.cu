@@ -1,5 +1,6 @@
-// lbm_batch_kernels.cu -- the batched step kernel and the batch's Nusselt
-// kernel (many cavities, one launch per step).
+// lbm_batch_kernels.cu -- the global-load batched step kernel and the
+// batch's Nusselt kernel (many cavities, one launch per step).  FP32 batches
+// of walled cavities run the staged kernel of lbm_step_tma.cu instead.
 #include <math.h>
 
 #include "lbm_step.cuh"
@@ -8,13 +9,9 @@ namespace lbm {
 
 // ------------------------------------------------------------------ batches
 
-// Batched step: a grid of resident blocks walks a work list of tiles drawn
-// from many cavities of different size and parameters.  Each block takes one
-// contiguous chunk of the list (items are sorted by cavity, so a block
-// changes cavity rarely) and stages the current cavity's constants in shared
-// memory; every node then runs the same interior / wall code as k_step.
-// Small cavities have many wall nodes; the batched kernel runs better with a
-// little more register room for their out-of-line path (6 x 128 threads).
+// Resident blocks per SM of the batched step.  Small cavities have many wall
+// nodes; the batched kernel runs better with a little more register room for
+// their out-of-line path (6 x 128 threads).
 #ifndef LBM_BATCH_BLOCKS
 #define LBM_BATCH_BLOCKS 6
 #endif
@@ -43,9 +40,9 @@ __device__ __forceinline__ void perimeter_node(const KConst<R>& k, int idx, int&
 // cavities of different size and parameters.  Each block takes one
 // contiguous, cost-balanced range of the list (items are sorted by cavity,
 // so a block changes cavity rarely) and stages the current cavity's
-// constants in shared memory.  Interior tiles and packed wall nodes are
-// separate items, so the out-of-line wall path never stalls a warp of
-// interior nodes.
+// constants in shared memory; every node runs the same interior / wall
+// code as k_step.  Interior tiles and packed wall nodes are separate items,
+// so the out-of-line wall path never stalls a warp of interior nodes.
 template <class R, class S, int TX>
 __global__ void __launch_bounds__(kStepBlock, BatchOccupancy<R>::blocks)
 k_step_batch(const BatchCavity<R>* __restrict__ cav, const BatchItem* __restrict__ items,
