@@ -4,7 +4,9 @@
 // per-node arithmetic of the step in registers, and one write of the 17
 // post-collision planes to the pong buffer.  Wall nodes take the NEES rebuild
 // inside the same launch (an out-of-line path that pulls the populations of
-// the wall node's fluid neighbour x_f instead of its own).
+// the wall node's fluid neighbour x_f instead of its own).  FP32 and FP16
+// lattices walled on all four sides run the kernel with TMA-staged rows
+// (lbm_step_tma.cu) unless the global-load kernel is selected.
 #include <math.h>
 
 #include "lbm_step.cuh"
