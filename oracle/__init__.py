@@ -52,15 +52,16 @@ def _compile(out: str, extra=()) -> str:
         return out
     os.makedirs(_OUT_DIR, exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99", *extra,
-                    "-o", tmp, _SRC, "-lm"], check=True)
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=c99",
+                    *extra, "-o", tmp, _SRC, "-lm"], check=True)
     os.replace(tmp, out)
     return out
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle into a shared library (plain gcc, -O2, no FMA
-    contraction, no target-specific flags), and its complex-step twin."""
+    contraction, no target-specific flags, OpenMP over the rows of a step),
+    and its complex-step twin."""
     with _lock:
         if force:
             for f in (_LIB_PATH, _CS_LIB_PATH):
@@ -94,6 +95,8 @@ def lib():
         L.orc_stream_function.argtypes = [C.c_int, C.c_int, dp, dp]
         L.orc_totals.argtypes = [P, dp, dp, dp]
         L.orc_set_ay_profile.argtypes = [vp, C.c_int]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_get_threads.argtypes = []
         _lib = L
     return _lib
 
@@ -114,6 +117,7 @@ def cs_lib():
         L.orc_moments.argtypes = [P, vp, cp, cp, vp, vp, vp, vp]
         L.orc_nusselt.argtypes = [P, cp, C.c_int, vp, vp]
         L.orc_set_ay_profile.argtypes = [vp, C.c_int]
+        L.orc_set_threads.argtypes = [C.c_int]
         _cs_lib = L
     return _cs_lib
 
@@ -165,6 +169,20 @@ def nusselt_gradient(p: dict, steps: int, eps_field, cells, sides=("W", "E"), h:
         d_t[side] = complex_step_nusselt(p, steps, base, tuple(im), T=T, ux=ux, uy=uy,
                                          side=loss_side).imag / h
     return np.array(d_eps), d_t
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads for the oracle's loops over nodes (0: one per processor, the
+    default); returns the count now in use.  The result of every call is the
+    same bit for bit whatever the count (each node of a step depends on the
+    previous state alone; sums stay single-threaded)."""
+    lib().orc_set_threads(int(n))
+    cs_lib().orc_set_threads(int(n))
+    return int(lib().orc_get_threads())
+
+
+def threads() -> int:
+    return int(lib().orc_get_threads())
 
 
 def set_ay_profile(ay, complex_build: bool = False):

@@ -54,6 +54,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* The same source builds twice: with real_t = double (the oracle), and with
  * real_t = double complex (-DORC_COMPLEX) for complex-step derivatives: a
@@ -174,6 +177,21 @@ typedef struct {
 } orc_state;
 
 static int is_nan(real_t v) { return v != v; }
+
+/* Threads for the loops over nodes.  Every node of a step is computed from
+ * the previous state alone and written to its own slots, so the rows may be
+ * shared among threads without changing a single bit of the result; the
+ * sums (totals, residual, Nusselt mean) stay single-threaded, in node order.
+ * 0 (the default) means one thread per processor. */
+static int g_threads = 0;
+int orc_set_threads(int n) { g_threads = n < 0 ? 0 : n; return 0; }
+int orc_get_threads(void) {
+#ifdef _OPENMP
+    return g_threads > 0 ? g_threads : omp_get_num_procs();
+#else
+    return 1;
+#endif
+}
 
 /* Derivation of the lattice constants.  U = Ma c_s is the characteristic
  * velocity of Sec. 4; g beta, nu and alpha_e invert the definitions of Ra and
@@ -661,9 +679,12 @@ int orc_init(const orc_problem *pb, const real_t *T, const real_t *ux, const rea
     int rc = make_ctx(pb, eps_field, &cx);
     if (rc) return rc;
     int nx = pb->nx, ny = pb->ny;
-    real_t S[2][2] = {{0, 0}, {0, 0}}, z[2] = {0, 0};
+    const int nth = orc_get_threads();
+    (void)nth;
+#pragma omp parallel for schedule(static) num_threads(nth)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
+            real_t S[2][2] = {{0, 0}, {0, 0}}, z[2] = {0, 0};
             size_t k = (size_t)y * nx + x;
             orc_cell c;
             node_cell(&cx, x, y, &c);
@@ -692,7 +713,10 @@ int orc_run(const orc_problem *pb, const real_t *eps_field, real_t *f, real_t *g
     real_t *g2 = (real_t *)malloc(tot * sizeof(real_t));
     if (!f2 || !g2) { free(f2); free(g2); return 100; }
     real_t *fa = f, *ga = g, *fb = f2, *gb = g2;
+    const int nth = orc_get_threads();
+    (void)nth;
     for (int64_t s = 0; s < n; ++s) {
+#pragma omp parallel for schedule(static) num_threads(nth)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 real_t fo[9], go[9];
@@ -718,6 +742,9 @@ int orc_update_nodes(const orc_problem *pb, const real_t *eps_field, const real_
     orc_ctx cx;
     int rc = make_ctx(pb, eps_field, &cx);
     if (rc) return rc;
+    const int nth = orc_get_threads();
+    (void)nth;
+#pragma omp parallel for schedule(static) num_threads(nth)
     for (int64_t k = 0; k < n; ++k) node_update(&cx, f, g, xs[k], ys[k], fo + 9 * k, go + 9 * k);
     return 0;
 }
@@ -730,6 +757,9 @@ int orc_moments(const orc_problem *pb, const real_t *eps_field, const real_t *f,
     int rc = make_ctx(pb, eps_field, &cx);
     if (rc) return rc;
     int nx = pb->nx, ny = pb->ny;
+    const int nth = orc_get_threads();
+    (void)nth;
+#pragma omp parallel for schedule(static) num_threads(nth)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             orc_state st;
@@ -751,6 +781,9 @@ int orc_gradients(const orc_problem *pb, const real_t *eps_field, const real_t *
     int rc = make_ctx(pb, eps_field, &cx);
     if (rc) return rc;
     int nx = pb->nx, ny = pb->ny;
+    const int nth = orc_get_threads();
+    (void)nth;
+#pragma omp parallel for schedule(static) num_threads(nth)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             orc_state st;
