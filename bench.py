@@ -39,6 +39,7 @@ BYTES_PER_CELL = {"f64": 17 * 8 * 2, "f32": 17 * 4 * 2, "f16": 17 * 2 * 2,
                   "f32/moments": 9 * 4 * 2, "f64/moments": 9 * 8 * 2}
 METRIC = "coupled flow+thermal MLUPS and % HBM roofline at 1 GB300 (plain FP32 fused step)"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_f32_2048_traffic.json")
+FP64_OPS_FILE = os.path.join(ROOT, "profiles", "step_f64_2048_fp64_ops.json")
 KERNEL_SOURCES = ("paper_1505_02976_gb300/csrc/lbm_device.cuh", "paper_1505_02976_gb300/csrc/lbm_step.cuh",
                   "paper_1505_02976_gb300/csrc/lbm_kernels.cu", "paper_1505_02976_gb300/csrc/lbm_step_tma.cu")
 
@@ -71,6 +72,21 @@ def ncu_traffic_per_launch():
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
     return float(d["dram_bytes_per_launch"])
+
+
+def ncu_fp64_record():
+    """FP64 operations per node of the FP64 step kernel (DFMA counted as two
+    FLOP, DADD and DMUL as one) and its FP64-pipe busy fraction, from the
+    committed ncu summary, or None when it was taken on a different kernel
+    source."""
+    try:
+        with open(FP64_OPS_FILE) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d
 
 
 # ----------------------------------------------------------------- clocks
@@ -166,13 +182,39 @@ def barrier(world: int, device=None):
 
 # ----------------------------------------------------------------- CPU legs
 
-def oracle_mlups(n: int, steps: int) -> tuple[float, float]:
-    """The FP64 CPU oracle as it stands on an n x n cavity with the workload's
-    groups: returns (MLUPS, seconds)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_cavity(n: int):
     import oracle
     from paper_1505_02976_gb300 import workloads as W
     p = W.cavity(n, WORKLOAD["Ra"], WORKLOAD["Da"], WORKLOAD["eps"], Pr=WORKLOAD["Pr"])
-    o = oracle.Oracle(p)
+    return oracle.Oracle(p)
+
+
+def oracle_mlups(n: int, steps: int, threads: int) -> tuple[float, float]:
+    """The FP64 CPU oracle as it stands on an n x n cavity with the workload's
+    groups, its loops over nodes shared by `threads` threads (0: all
+    processors): returns (MLUPS, seconds) of one run of `steps` steps."""
+    import oracle
+    oracle.set_threads(threads)
+    o = oracle_cavity(n)
     t0 = time.perf_counter()
     o.run(steps)
     dt = time.perf_counter() - t0
@@ -180,40 +222,56 @@ def oracle_mlups(n: int, steps: int) -> tuple[float, float]:
 
 
 def cpu_baseline_leg() -> dict:
-    n, steps = WORKLOAD["n"], 2
-    v, dt = oracle_mlups(n, steps)
-    return {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{n}x{n} cavity (the benchmark workload), {steps} time steps, "
-                      f"single-threaded FP64 oracle, {dt:.1f} s"}
+    """The oracle on this host's cores, on the benchmark workload itself: one
+    run single-threaded and one on every processor (nproc)."""
+    import oracle
+    n = WORKLOAD["n"]
+    nproc = os.cpu_count() or 1
+    runs = []
+    for threads, steps in ((1, 2), (nproc, 12)):
+        v, dt = oracle_mlups(n, steps, threads)
+        runs.append({"threads": oracle.threads(), "value": v, "unit": "MLUPS", "steps": steps,
+                     "seconds": dt})
+    oracle.set_threads(0)
+    best = runs[-1]
+    return {"value": best["value"], "unit": "MLUPS", "cores": best["threads"], "kind": "oracle",
+            "cpu_model": cpu_model(), "nproc": nproc,
+            "sample": f"{n}x{n} cavity (the benchmark workload): {runs[0]['steps']} time steps on "
+                      f"1 thread ({runs[0]['seconds']:.1f} s) and {best['steps']} on "
+                      f"{best['threads']} threads ({best['seconds']:.1f} s), FP64 oracle",
+            "runs": runs}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the benchmark workload itself
+    (the same 2048 x 2048 cavity and groups), every host processor, one full
+    oracle time step per benchmark step; W steps of warm-up, then K timed
+    steps in one run."""
+    import oracle
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    n = 512
-    for _ in range(args.warmup):
-        oracle_mlups(n, 1)
-    t0 = time.perf_counter()
-    import oracle
-    from paper_1505_02976_gb300 import workloads as W
-    p = W.cavity(n, WORKLOAD["Ra"], WORKLOAD["Da"], WORKLOAD["eps"], Pr=WORKLOAD["Pr"])
-    o = oracle.Oracle(p)
+    n = WORKLOAD["n"]
+    oracle.set_threads(0)
+    o = oracle_cavity(n)
+    o.run(args.warmup)
     t0 = time.perf_counter()
     o.run(args.steps)
     dt = time.perf_counter() - t0
     v = n * n * args.steps / dt / 1e6
+    cores = oracle.threads()
+    sample = (f"{n}x{n} cavity (the benchmark workload), {args.steps} oracle time steps after "
+              f"{args.warmup} of warm-up, {cores} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"], "nx": WORKLOAD["n"], "ny": WORKLOAD["n"],
+        "config": {"workload": WORKLOAD["name"], "nx": n, "ny": n,
                    "Ra": WORKLOAD["Ra"], "Da": WORKLOAD["Da"], "eps": WORKLOAD["eps"],
-                   "Pr": WORKLOAD["Pr"], "reference_sample": f"{n}x{n} cavity, same groups"},
-        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"{n}x{n} cavity with the workload's groups, one oracle time "
-                                   f"step per benchmark step, single thread"},
+                   "Pr": WORKLOAD["Pr"], "storage": "f64 (oracle)", "state": "populations"},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -263,12 +321,32 @@ def variant_lines(device, local, warmup: int, steps: int) -> dict:
                      "ms_per_step": 1e3 * loop / steps, "kernel_ms": 1e3 * kernel,
                      "hbm_gbs": gbs, "hbm_frac": gbs / peak,
                      "bytes_per_node": BYTES_PER_CELL[key]}
+        if prec == "f64":
+            out[name]["roofline"] = fp64_roofline(stream, cells, kernel)
         lat.close()
         del lat
         torch.cuda.empty_cache()
     out["batch512_fp32"] = batch_line(device, local, peak)
     out["adjoint256_fp32"] = adjoint_line(device, local)
     return out
+
+
+def fp64_roofline(stream, cells: int, kernel_s: float) -> dict:
+    """The FP64 step against the FP64 pipe: FP64 FLOP per node from the ncu
+    summary (executed DFMA x 2 + DADD + DMUL, per node of one launch) times
+    the nodes, over the live mean launch time, against the FP64 FMA rate
+    measured on this GPU by lbm_fp64_peak."""
+    from paper_1505_02976_gb300 import lbm
+    peak = lbm.fp64_peak(stream) / 1e12
+    rec = ncu_fp64_record()
+    if rec is None:
+        return {"bound": "fp64", "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
+                "peak_kind": "measured (lbm_fp64_peak)", "note": "no ncu FP64 count for this kernel source"}
+    achieved = rec["fp64_flop_per_node"] * cells / kernel_s / 1e12
+    return {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "peak_kind": "measured (lbm_fp64_peak)",
+            "fp64_flop_per_node": rec["fp64_flop_per_node"],
+            "ncu_fp64_pipe_busy": rec.get("fp64_pipe_busy")}
 
 
 def adjoint_line(device, local) -> dict:

@@ -231,6 +231,15 @@ lbm_status lbm_check_guards(lbm_handle* h);
  * lbm_set_state clear the status.  Asynchronous. */
 lbm_status lbm_wait_selftest(lbm_handle* h);
 
+/* FP64 throughput of the device (the paper has no counterpart; a
+ * measurement helper): runs, on the given stream (a cudaStream_t, NULL = the
+ * legacy default stream), a kernel of independent FP64 fused multiply-add
+ * chains filling every SM, times it with CUDA events and stores the rate in
+ * FLOP/s (one FMA = 2 FLOP) in *flops_per_s (host).  The FP64 step is bound
+ * by this rate, not by memory; it is the denominator of that step's
+ * roofline.  Synchronises the stream; LBM_ERR_CUDA on any CUDA failure. */
+lbm_status lbm_fp64_peak(void* stream, double* flops_per_s);
+
 /* Macroscopic fields of the current state: the pressure, velocity and
  * temperature that the next step computes after streaming (Sec. 3.1-3.2);
  * wall nodes report their boundary state (u_b, T_b, p(x_f)) of Sec. 3.4.
@@ -254,11 +263,10 @@ lbm_status lbm_nusselt(lbm_handle* h, int side, double* nu_mean, double* nu_loca
  * The paper has no counterpart to this entry point.  It allocates nothing:
  * the per-node values live in a fixed array compiled into the library (held
  * on every GPU that loads it until exit), so the wall may have at most 65536
- * nodes (else LBM_ERR_ARG).  The first call on a device looks up that
- * array's device address; make that first call before any stream capture.
- * All calls share the array: calls whose GPU work overlaps (other streams or
- * other handles on the same device) race.  nu_mean: host pointer.
- * Synchronises the handle's stream. */
+ * nodes (else LBM_ERR_ARG).  Every call looks up that array's device
+ * address on the device of the handle's stream.  All calls share the array:
+ * calls whose GPU work overlaps (other streams or other handles on the same
+ * device) race.  nu_mean: host pointer.  Synchronises the handle's stream. */
 lbm_status lbm_nusselt_noalloc(lbm_handle* h, int side, double* nu_mean);
 
 /* Steady-state criterion of Sec. 4 against the snapshot taken by the
@@ -309,10 +317,14 @@ lbm_status lbm_adjoint(lbm_handle* h, int64_t n_steps, int64_t segment, int side
  * porosity field and step counter.  The file holds a header (format tag,
  * precision, lattice shape, a hash of the lbm_params the handle was created
  * with), the raw stored planes and a CRC-32 of them; a restore checks all of
- * them and fails with LBM_ERR_ARG on any mismatch or corruption, leaving the
- * state unchanged.  A restored run continues bit for bit as the saved one
- * would have.  The force profile of lbm_set_force_profile is not part of the
- * file: set it again on the restoring handle.  Synchronises. */
+ * them on the host before it touches the device and fails with LBM_ERR_ARG
+ * on any mismatch or corruption, leaving the state unchanged.  (A CUDA
+ * failure while the checked payload is copied to the device returns
+ * LBM_ERR_CUDA and leaves the state undefined.)  A restored run continues
+ * bit for bit as the saved one would have.  Neither the force profile of
+ * lbm_set_force_profile nor the residual snapshot is part of the file: set
+ * the profile again on the restoring handle; the restored state becomes the
+ * reference of the next lbm_residual.  Synchronises. */
 lbm_status lbm_checkpoint(lbm_handle* h, const char* path, int save);
 
 /* Steps completed since the last lbm_set_fields. */

@@ -7,7 +7,6 @@
 #include <stdlib.h>
 #include <string.h>
 
-#include <mutex>
 #include <vector>
 #include <new>
 #include <type_traits>
@@ -693,6 +692,11 @@ lbm_status lbm_checkpoint(lbm_handle* h, const char* path, int save) {
     h->steps = hd.steps;
     h->nonfinite = false;
     h->timeout = false;
+    // the residual snapshot is not part of the file: the restored state
+    // becomes the reference of the next lbm_residual
+    lbm_status s = reset_snapshot(h);
+    if (s != LBM_OK) return s;
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "residual snapshot of the restored state");
     return LBM_OK;
 }
 
@@ -725,27 +729,20 @@ static constexpr int kNoAllocMaxNodes = 65536;
 static __device__ __align__(256) double g_nu_scratch[kNoAllocMaxNodes + 32];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_nu_scratch_mu;
-double* g_nu_scratch_ptr[kMaxDevices];  // device address of the array, per device
-
-// Device address of the scratch array on `device`, looked up once per device
-// with that device current.  In host code g_nu_scratch names a host-side
-// stand-in, not device memory; only this address may be given to a kernel.
+// Device address of the scratch array on `device`, looked up on every call
+// with that device current (the lookup is cheap, and nothing is cached that
+// a device reset could leave stale).  In host code g_nu_scratch names a
+// host-side stand-in, not device memory; only this address may be given to
+// a kernel.
 lbm_status nu_scratch_on(lbm_handle* h, int device, double** out) {
-    if (device < 0 || device >= kMaxDevices) return fail(h, LBM_ERR_ARG, "device ordinal out of range");
-    std::lock_guard<std::mutex> lock(g_nu_scratch_mu);
-    if (!g_nu_scratch_ptr[device]) {
-        int prev = -1;
-        LBM_CUDA(h, cudaGetDevice(&prev), "current device");
-        if (prev != device) LBM_CUDA(h, cudaSetDevice(device), "select the stream's device");
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_nu_scratch);
-        if (prev != device) cudaSetDevice(prev);
-        if (e != cudaSuccess) return cuda_fail(h, e, "address of the static Nusselt scratch");
-        g_nu_scratch_ptr[device] = (double*)p;
-    }
-    *out = g_nu_scratch_ptr[device];
+    int prev = -1;
+    LBM_CUDA(h, cudaGetDevice(&prev), "current device");
+    if (prev != device) LBM_CUDA(h, cudaSetDevice(device), "select the stream's device");
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_nu_scratch);
+    if (prev != device) cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "address of the static Nusselt scratch");
+    *out = (double*)p;
     return LBM_OK;
 }
 }  // namespace

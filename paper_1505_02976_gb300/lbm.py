@@ -33,7 +33,7 @@ EXPORTED = ("lbm_params_default", "lbm_derived", "lbm_workspace_size", "lbm_crea
             "lbm_adjoint", "lbm_totals", "lbm_checkpoint", "lbm_set_force_profile",
             "lbm_stream_function", "lbm_set_moment_segments", "lbm_wait_selftest",
             "lbm_set_step_staging", "lbm_step_staged", "lbm_batch_set_staging", "lbm_batch_staged",
-            "lbm_check_guards", "lbm_batch_check_guards")
+            "lbm_check_guards", "lbm_batch_check_guards", "lbm_fp64_peak")
 BATCH_MODE = {"fused": 0, "graph": 1, "per_case": 2}
 
 
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
     L.lbm_set_force_profile.argtypes = [H, C.c_void_p]
     L.lbm_stream_function.argtypes = [H, C.c_void_p, C.c_int, C.c_void_p]
     L.lbm_set_moment_segments.argtypes = [H, C.c_int32]
+    L.lbm_fp64_peak.argtypes = [C.c_void_p, dp]
     B = C.c_void_p
     L.lbm_batch_set_staging.argtypes = [B, C.c_int32]
     L.lbm_batch_staged.argtypes = [B]
@@ -478,6 +479,15 @@ class Batch:
     @property
     def cells(self) -> int:
         return sum(int(p["nx"]) * int(p["ny"]) for p in self.problems)
+
+
+def fp64_peak(stream=None) -> float:
+    """FP64 fused multiply-add throughput of the stream's device, FLOP/s
+    (lbm_fp64_peak)."""
+    out = C.c_double()
+    s = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(load().lbm_fp64_peak(s, C.byref(out)))
+    return out.value
 
 
 def mlups(nx: int, ny: int, steps: int, seconds: float) -> float:

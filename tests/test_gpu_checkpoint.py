@@ -51,3 +51,25 @@ def test_corrupted_or_foreign_checkpoint_is_refused(tmp_path):
         other.load_checkpoint(str(path))
     with pytest.raises(lbm.LbmError):
         lbm.Lattice(p, "f64").load_checkpoint(str(path))
+
+
+def test_restore_makes_the_restored_state_the_residual_reference(tmp_path):
+    """The residual snapshot is not part of the file: after a restore, the
+    next lbm_residual compares against the restored state, so a residual
+    taken straight after the restore is zero, and one taken after some steps
+    equals the one the saved run reports after the same steps."""
+    p = W.cavity(40, 1e5, 1e-2, 0.6)
+    g = lbm.Lattice(p, "f64")
+    g.step(200)
+    path = str(tmp_path / "c.ckpt")
+    g.save(path)
+    g.residual()          # snapshot = the saved state
+    g.step(30)
+    ref = g.residual()
+    h = lbm.Lattice(p, "f64")
+    h.step(500)           # a different state and snapshot before the restore
+    h.residual()
+    h.load_checkpoint(path)
+    assert h.residual() == (0.0, 0.0)
+    h.step(30)
+    assert h.residual() == ref
