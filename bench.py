@@ -44,9 +44,12 @@ KERNEL_SOURCES = ("paper_1505_02976_gb300/csrc/lbm_device.cuh", "paper_1505_0297
                   "paper_1505_02976_gb300/csrc/lbm_kernels.cu", "paper_1505_02976_gb300/csrc/lbm_step_tma.cu")
 
 
-def kernel_source_hash() -> str:
+FP64_KERNEL_SOURCES = KERNEL_SOURCES[:3]   # k_step<double, double> does not use the staged kernel's file
+
+
+def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in sources:
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -84,7 +87,7 @@ def ncu_fp64_record():
             d = json.load(fh)
     except Exception:
         return None
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    if d.get("kernel_source_hash") != kernel_source_hash(FP64_KERNEL_SOURCES):
         return None
     return d
 
