@@ -131,6 +131,25 @@ def test_fp64_adjoint_against_central_differences_full_size():
     print(f"nodes above the floor (|fd| > {floor / 1e-4:.0e}): {(np.abs(fd) * 1e-4 > floor).sum()} of {len(fd)}; "
           f"largest relative error there {rel[np.abs(fd) * 1e-4 > floor].max():.2e}")
     assert (err <= np.maximum(1e-4 * np.abs(fd), floor)).all(), (rel.max(), err.max())
+    # Richardson pair at larger steps: (4 D(h/2) - D(h)) / 3 with h = 2e-3
+    # cancels the h^2 truncation term (the remainder, h^4 over (1 - eps)^4 at
+    # eps <= 0.9, stays below 1e-6 relative) and divides the round-off floor
+    # by 20, so most sampled nodes are checked at 1e-4 relative.
+    def central(x, y, hh):
+        ep, em = eps.copy(), eps.copy()
+        ep[y, x] += hh
+        em[y, x] -= hh
+        return (_nu64(p, ep, steps) - _nu64(p, em, steps)) / (2 * hh)
+    hr = 2e-3
+    fdr = np.array([(4 * central(x, y, hr / 2) - central(x, y, hr)) / 3 for x, y in cells])
+    floor_r = 1e-11
+    err_r = np.abs(ad - fdr)
+    rel_r = err_r / np.maximum(np.abs(fdr), 1e-300)
+    above = np.abs(fdr) * 1e-4 > floor_r
+    print(f"Richardson (h = {hr}, {hr / 2}): nodes above the floor (|fd| > {floor_r / 1e-4:.0e}): "
+          f"{above.sum()} of {len(fdr)}; largest relative error there {rel_r[above].max():.2e}; "
+          f"all relative errors: {np.array2string(rel_r, precision=1)}")
+    assert (err_r <= np.maximum(1e-4 * np.abs(fdr), floor_r)).all(), (rel_r.max(), err_r.max())
     fd_h = (_nu64(p, eps, steps, Th=1 + h) - _nu64(p, eps, steps, Th=1 - h)) / (2 * h)
     fd_c = (_nu64(p, eps, steps, Tc=h) - _nu64(p, eps, steps, Tc=-h)) / (2 * h)
     assert g_t[0] == pytest.approx(fd_h, rel=1e-4)

@@ -60,11 +60,14 @@ def test_fp32_2048_cavity_after_100000_steps():
     nu_hot, loc_hot = g.nusselt("W")
     nu_cold, _ = g.nusselt("E")
     tau = 100_000 * d["alpha_e"] / d["L"] ** 2
-    # pure conduction from a suddenly heated wall would give Nu = 1/sqrt(pi tau)
-    nu_cond = 1.0 / np.sqrt(np.pi * tau)
+    # pure conduction into a half-space whose wall jumps from T_init to Th:
+    # Nu = (Th - T_init) / (Th - Tc) / sqrt(pi tau)
+    nu_cond = (p["Th"] - p["T_init"]) / (p["Th"] - p["Tc"]) / np.sqrt(np.pi * tau)
     print(f"\n2048^2 FP32, 100000 steps: t alpha_e / L^2 = {tau:.4e}; Nu hot {nu_hot:.6f}, "
           f"Nu cold {nu_cold:.6f}; conduction-only estimate {nu_cond:.4f}; paper's steady value 2.618")
     assert np.isfinite(loc_hot).all()
     assert nu_hot > 2.618 and nu_cold > 2.618
-    # convection only thins the hot-wall boundary layer relative to conduction
-    assert nu_hot > 0.9 * nu_cond
+    # at this early time the wall layers are still close to conduction;
+    # convection only thins them
+    assert nu_cond * 0.99 < nu_hot < 1.2 * nu_cond
+    assert abs(nu_hot - nu_cold) < 1e-3 * nu_hot
