@@ -45,25 +45,48 @@ constexpr int kTRows = LBM_TMA_ROWS;  // output rows staged per block (the segme
 constexpr unsigned long long kTWaitNs = 2000000000ull;  // a wait gives up after 2 s
 constexpr long long kTWaitPolls = 1ll << 28;             // ... or after this many polls
 
-// Shared-memory layout of the staged rows for storage type S.  A copy starts
-// `halo` columns left of the band so that its x coordinate stays a multiple
-// of 16 bytes; a copy's shared-memory destination must be 128-byte aligned,
-// so each plane row of a slot is padded to a multiple of 128 bytes.
-template <class S>
-struct TmaLayout {
+// Shared-memory layout of the staged rows: storage type S, BAND output
+// columns per block, ROWS output rows.  A copy starts `halo` columns left of
+// the band so that its x coordinate stays a multiple of 16 bytes; a copy's
+// shared-memory destination must be 128-byte aligned, so each plane row of a
+// slot is padded to a multiple of 128 bytes.
+template <class S, int BAND, int ROWS>
+struct StageLayout {
+    using type = S;
+    static constexpr int band = BAND;
+    static constexpr int rows = ROWS;
     static constexpr int halo = 16 / (int)sizeof(S);                        // 4 (FP32), 8 (FP16)
-    static constexpr int box = kTBand + 2 * halo;                           // 136, 144 columns
-    static constexpr int plane = ((box * (int)sizeof(S) + 127) / 128) * 128 / (int)sizeof(S);  // 160, 192
+    static constexpr int box = BAND + 2 * halo;                             // columns copied per plane row
+    static constexpr int plane = ((box * (int)sizeof(S) + 127) / 128) * 128 / (int)sizeof(S);
     static constexpr int slot = NPLANES * plane;                            // elements per slot
     static constexpr unsigned bytes = (unsigned)(NPLANES * box * sizeof(S));  // bytes landing per slot
     // slots, barriers, and room to round the first slot up to 128 bytes
-    static constexpr size_t smem = 128 + (size_t)kTRows * slot * sizeof(S) + kTRows * sizeof(uint64_t);
+    static constexpr size_t smem = 128 + (size_t)ROWS * slot * sizeof(S) + ROWS * sizeof(uint64_t);
     // resident blocks per SM that the shared memory allows (228 KB per SM,
     // 1 KB reserved per block), at most 8
     static constexpr int blocks = (int)((228 * 1024) / (smem + 1024)) < 8 ? (int)((228 * 1024) / (smem + 1024)) : 8;
+    static_assert(plane * sizeof(S) % 128 == 0, "plane rows must stay 128-byte aligned");
 };
-static_assert(TmaLayout<float>::plane * sizeof(float) % 128 == 0, "plane rows must stay 128-byte aligned");
-static_assert(TmaLayout<__half>::plane * sizeof(__half) % 128 == 0, "plane rows must stay 128-byte aligned");
+// FP32 storage: one node per thread, a band of 128 columns, kTRows rows.
+template <class S> struct TmaLayoutOf;
+template <> struct TmaLayoutOf<float> { using type = StageLayout<float, kTBand, kTRows>; };
+// FP16 storage: two x-adjacent nodes per thread (one pair per thread), a
+// band of 256 columns, kHRows rows.
+#ifndef LBM_TMA_ROWS_H
+#define LBM_TMA_ROWS_H 2
+#endif
+constexpr int kHRows = LBM_TMA_ROWS_H;
+template <> struct TmaLayoutOf<__half> { using type = StageLayout<__half, 2 * kTBand, kHRows>; };
+template <class S> using TmaLayout = typename TmaLayoutOf<S>::type;
+// Resident blocks per SM the kernels are compiled for (registers: 65536 /
+// (threads x blocks) each): FP16 threads carry two nodes.
+#ifndef LBM_TMA_BLOCKS_H
+#define LBM_TMA_BLOCKS_H 6
+#endif
+template <class S> struct TmaBlocks { static constexpr int value = TmaLayout<S>::blocks; };
+template <> struct TmaBlocks<__half> {
+    static constexpr int value = TmaLayout<__half>::blocks < LBM_TMA_BLOCKS_H ? TmaLayout<__half>::blocks : LBM_TMA_BLOCKS_H;
+};
 
 // Source row offset (-c_iy) and column offset (-c_ix) of each stored plane:
 // planes 0..7 hold f_1..f_8, planes 8..16 h_0..h_8; c: 1 (+1,0) 2 (0,+1)
@@ -131,9 +154,9 @@ template <class S>
 __device__ __forceinline__ void staged_setup(unsigned char* smem_raw, S*& stage, uint64_t*& bar) {
     unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     stage = reinterpret_cast<S*>(base);
-    bar = reinterpret_cast<uint64_t*>(base + (size_t)kTRows * TmaLayout<S>::slot * sizeof(S));
+    bar = reinterpret_cast<uint64_t*>(base + (size_t)TmaLayout<S>::rows * TmaLayout<S>::slot * sizeof(S));
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kTRows; ++s)
+        for (int s = 0; s < TmaLayout<S>::rows; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar + s)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -219,12 +242,116 @@ __device__ __forceinline__ void staged_rows(const KConst<float>& k, const S* __r
     }
 }
 
+// The FP16 form of staged_rows: one pair of x-adjacent nodes per thread,
+// columns x0 + 2 tid (node a) and x0 + 2 tid + 1 (node b) of a band of 256
+// columns.  Node a's slot column c is even, so each plane's two pulled
+// values come from one aligned 32-bit word (no x shift) or from the halves
+// of two neighbouring words (shift of one column); they are packed into one
+// half2 per plane, node a in the lower half.  Both nodes' 17 values are then
+// stored as pairs: one stochastic-rounding conversion and one 32-bit store
+// per plane (a pair with a wall or out-of-range member stores its interior
+// node alone, with the same rounding).
+template <bool EPS_FIELD, bool TAU1>
+__device__ __forceinline__ void staged_rows_pair(const KConst<float>& k, const __half* __restrict__ src,
+                                                 __half* __restrict__ dst, int x0, int y0, int rows, uint32_t step,
+                                                 const __half* stage, uint64_t* bar) {
+    using L = TmaLayout<__half>;
+    const int tid = threadIdx.x;
+    const int y1 = min(y0 + rows, k.ny);
+    const int yb = max(y0, 1), ye = min(y1, k.ny - 1);  // interior rows of the segment
+    const int xa = x0 + 2 * tid;
+    // wall nodes of the segment, in parallel, while the copies fly
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (xa + q < k.nx) {
+            if (y0 == 0) wall_update(k, src, dst, xa + q, 0, step);
+            if (y1 == k.ny) wall_update(k, src, dst, xa + q, k.ny - 1, step);
+        }
+    }
+    if (x0 == 0)
+        for (int y = yb + tid; y < ye; y += kTBand) wall_update(k, src, dst, 0, y, step);
+    if (x0 <= k.nx - 1 && k.nx - 1 < x0 + L::band)
+        for (int y = yb + tid; y < ye; y += kTBand) wall_update(k, src, dst, k.nx - 1, y, step);
+    const bool act0 = xa >= 1 && xa <= k.nx - 2;
+    const bool act1 = xa + 1 <= k.nx - 2;
+    const int c = 2 * tid + L::halo;
+    // the storage scale folds into the collision weights at tau = 1
+    const float out_scale = TAU1 ? 1.0f : k.inv_scale;
+    bool ok = true;
+    for (int y = yb; y < ye && (act0 || act1 || tid == 0); ++y) {
+        if (!tma_wait(bar + (y - yb), 0u)) {
+            ok = false;
+            break;
+        }
+        if (!(act0 || act1)) continue;
+        const __half* sl = stage + (y - yb) * L::slot + c;
+        __half2 pk[NPLANES];
+#pragma unroll
+        for (int p = 0; p < NPLANES; ++p) {
+            const __half* q = sl + p * L::plane;
+            if (plane_dx(p) == 0) {
+                pk[p] = *reinterpret_cast<const __half2*>(q);
+            } else if (plane_dx(p) < 0) {
+                const __half2 w0 = *reinterpret_cast<const __half2*>(q - 2);
+                const __half2 w1 = *reinterpret_cast<const __half2*>(q);
+                pk[p] = __halves2half2(__high2half(w0), __low2half(w1));
+            } else {
+                const __half2 w0 = *reinterpret_cast<const __half2*>(q);
+                const __half2 w1 = *reinterpret_cast<const __half2*>(q + 2);
+                pk[p] = __halves2half2(__high2half(w0), __low2half(w1));
+            }
+        }
+        float fo[2][9], ho[2][9];
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+            if (!(n == 0 ? act0 : act1)) continue;
+            float f[9], h[9];
+#pragma unroll
+            for (int i = 1; i < 9; ++i) f[i] = (n == 0 ? __low2float(pk[i - 1]) : __high2float(pk[i - 1])) * k.scale;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) h[i] = (n == 0 ? __low2float(pk[8 + i]) : __high2float(pk[8 + i])) * k.scale;
+            auto collide = [&](const KConst<float>& kk) {
+                const FastState<float> st = fast_moments(kk, f, h, y);
+                if constexpr (TAU1) fast_collide<float, true>(kk, st, f, h, fo[n], ho[n], kk.inv_scale);
+                else fast_collide<float, false>(kk, st, f, h, fo[n], ho[n]);
+            };
+            if constexpr (EPS_FIELD) {
+                KConst<float> kc = k;
+                apply_eps(kc, node_eps(k, xa + n, y));
+                collide(kc);
+            } else {
+                collide(k);
+            }
+        }
+        const int at = y * k.pitch + xa;
+        if (act0 && act1) {
+            const Dither dither((uint32_t)at, step);
+            store_pair_half<float>(dst + at, k.plane32, fo[0], ho[0], fo[1], ho[1], out_scale, dither);
+        } else {
+            if (act0) {
+                Dither d0((uint32_t)at, step);
+                store_planes_half<float>(dst + at, k.plane32, fo[0], ho[0], out_scale, &d0);
+            }
+            if (act1) {
+                Dither d1((uint32_t)(at + 1), step);
+                store_planes_half<float>(dst + at + 1, k.plane32, fo[1], ho[1], out_scale, &d1);
+            }
+        }
+    }
+    if (!ok) {
+        atomicOr(k.flag, 2);
+        // let this block's copies land before its shared memory is released
+        if (tid == 0)
+            for (int r = yb; r < ye; ++r) (void)tma_wait(bar + (r - yb), 0u);
+    }
+}
+
 // The staged step of one lattice: block (bx, by) owns band bx and a segment
 // of `rows` rows.  The two segments holding the S and N wall rows (a full row
 // of out-of-line wall updates each) are taken by the first two block rows,
 // so that the blocks the hardware starts last are plain interior ones.
 template <class S, bool EPS_FIELD, bool TAU1>
-__global__ void __launch_bounds__(kTBand, TmaLayout<S>::blocks)
+__global__ void __launch_bounds__(kTBand, TmaBlocks<S>::value)
 k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUtensorMap tm,
            const S* __restrict__ src, S* __restrict__ dst, int rows, uint32_t step) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -234,12 +361,15 @@ k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUte
     staged_setup<S>(smem_raw, stage, bar);
     const int by = (int)blockIdx.y, nseg = (int)gridDim.y;
     const int seg = by == 0 ? 0 : (by == 1 ? nseg - 1 : by - 1);
-    const int x0 = blockIdx.x * kTBand, y0 = seg * rows;
+    const int x0 = blockIdx.x * TmaLayout<S>::band, y0 = seg * rows;
     __syncthreads();  // barriers initialised (the other threads go on while thread 0 issues)
     // the previous step's writes must be visible before the first copy
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if (threadIdx.x == 0) staged_issue<S>(&tm, stage, bar, x0, y0, rows, k.ny);
-    staged_rows<S, EPS_FIELD, TAU1>(k, src, dst, x0, y0, rows, step, stage, bar);
+    if constexpr (std::is_same<S, __half>::value)
+        staged_rows_pair<EPS_FIELD, TAU1>(k, src, dst, x0, y0, rows, step, stage, bar);
+    else
+        staged_rows<S, EPS_FIELD, TAU1>(k, src, dst, x0, y0, rows, step, stage, bar);
 }
 
 // The staged step of a batch of FP32 cavities walled on all four sides: block
@@ -360,9 +490,11 @@ static cudaError_t launch_tma(const cudaLaunchConfig_t& cfg, const KConst<float>
 template <class S>
 cudaError_t launch_step_tma(const KConst<float>& k, const CUtensorMap& tm, const S* src, S* dst, int rows,
                             uint32_t step, cudaStream_t st) {
-    if (rows < 1 || rows > kTRows) return cudaErrorInvalidValue;
+    if (rows < 1) return cudaErrorInvalidValue;
+    if (rows > TmaLayout<S>::rows) rows = TmaLayout<S>::rows;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)((k.nx + kTBand - 1) / kTBand), (unsigned)((k.ny + rows - 1) / rows));
+    cfg.gridDim = dim3((unsigned)((k.nx + TmaLayout<S>::band - 1) / TmaLayout<S>::band),
+                       (unsigned)((k.ny + rows - 1) / rows));
     cfg.blockDim = dim3(kTBand);
     cfg.dynamicSmemBytes = TmaLayout<S>::smem;
     cfg.stream = st;
