@@ -347,7 +347,11 @@ typedef enum {
     LBM_BATCH_FUSED = 0,     /* one kernel launch per step for all cavities */
     LBM_BATCH_GRAPH = 1,     /* the same launches replayed from a captured CUDA graph
                                 (50 steps per graph; needs a non-default stream) */
-    LBM_BATCH_PER_CASE = 2   /* one single-lattice launch per cavity per step */
+    LBM_BATCH_PER_CASE = 2,  /* one single-lattice launch per cavity per step */
+    LBM_BATCH_PERSISTENT = 3 /* every step of the call in one cooperative launch: each resident
+                                block keeps taking (cavity, band, segment) items and waits,
+                                bounded, only until the item's neighbours have finished the
+                                previous step (staged batches only, else LBM_ERR_ARG) */
 } lbm_batch_mode;
 
 /* Bytes of device workspace for the n cavities of p[0..n-1]. */

@@ -52,6 +52,10 @@ struct lbm_batch {
     // maps of every cavity in both buffers (device: maps[buffer * n + c])
     bool staged, staged_ready;
     size_t off_maps, off_sitems;
+    // the persistent form of the staged step: its work list (cavity by
+    // cavity, segment-major), the per-cavity layout of that list, and the
+    // per-item step counters and abort word of a call
+    size_t off_pitems, off_pcav, off_done;
     std::vector<size_t> guards;        // offsets of the guard words after each region
     int n_sitems;
     std::vector<CUtensorMap> hmaps[2];
@@ -67,6 +71,9 @@ struct lbm_batch {
     int* bounds() const { return (int*)(ws + off_bounds); }
     const CUtensorMap* maps(int buffer) const { return (const CUtensorMap*)(ws + off_maps) + (size_t)buffer * n; }
     const lbm::StagedItem* sitems() const { return (const lbm::StagedItem*)(ws + off_sitems); }
+    const lbm::StagedItem* pitems() const { return (const lbm::StagedItem*)(ws + off_pitems); }
+    const lbm::PersistCavity* pcav() const { return (const lbm::PersistCavity*)(ws + off_pcav); }
+    int* done() const { return (int*)(ws + off_done); }
     size_t es() const { return precision == LBM_F64 ? 8 : 4; }
 };
 
@@ -153,6 +160,22 @@ std::vector<lbm::StagedItem> make_staged_items(const std::vector<lbm_params>& pr
     return walls;
 }
 
+// Work list of the persistent staged step: every cavity's segments of `rows`
+// rows x bands of 128 columns, cavity by cavity, segment-major, and the
+// position of each cavity's items in it.
+std::vector<lbm::StagedItem> make_persist_items(const std::vector<lbm_params>& prm, int rows,
+                                                std::vector<lbm::PersistCavity>* pc) {
+    std::vector<lbm::StagedItem> v;
+    if (pc) pc->clear();
+    for (int c = 0; c < (int)prm.size(); ++c) {
+        const int nb = (prm[c].nx + 127) / 128, ns = (prm[c].ny + rows - 1) / rows;
+        if (pc) pc->push_back({(int)v.size(), nb, ns, 0});
+        for (int g = 0; g < ns; ++g)
+            for (int bd = 0; bd < nb; ++bd) v.push_back({c, bd * 128, g * rows, prm[c].ny});
+    }
+    return v;
+}
+
 // Block ranges of equal estimated cost: bounds[k] is the first item of block k.
 std::vector<int> make_bounds(const std::vector<double>& cum, int grid) {
     const int n = (int)cum.size() - 1;
@@ -210,13 +233,16 @@ lbm_status batch_layout(const lbm_params* p, int n, lbm_batch* b, std::string* w
     }
     b->off_bounds = take((size_t)(kMaxGrid + 1) * sizeof(int));
     b->n_sitems = 0;
-    b->off_maps = b->off_sitems = o;
+    b->off_maps = b->off_sitems = b->off_pitems = b->off_pcav = b->off_done = o;
     if (stageable(b->prm)) {
         const size_t ns = make_staged_items(b->prm, lbm::tma_batch_rows()).size();
         if (ns >= (size_t)1 << 31) { *why = "batch too large"; return LBM_ERR_ARG; }
         b->n_sitems = (int)ns;
         b->off_maps = take((size_t)2 * n * sizeof(CUtensorMap));
         b->off_sitems = take(ns * sizeof(lbm::StagedItem));
+        b->off_pitems = take(ns * sizeof(lbm::StagedItem));
+        b->off_pcav = take((size_t)n * sizeof(lbm::PersistCavity));
+        b->off_done = take((ns + 1) * sizeof(int));
     }
     b->off_fields = take(4 * b->max_cells * sizeof(double));
     b->off_nu = take((size_t)n * sizeof(double));
@@ -423,6 +449,11 @@ lbm_status lbm_batch_create(const lbm_params* p, int32_t n, void* stream, void* 
         if (ok) {
             std::vector<lbm::StagedItem> it = make_staged_items(b->prm, lbm::tma_batch_rows());
             s = upload(b->off_sitems, it.data(), it.size() * sizeof(lbm::StagedItem), "staged work list");
+            std::vector<lbm::PersistCavity> pc;
+            std::vector<lbm::StagedItem> pit = make_persist_items(b->prm, lbm::tma_batch_rows(), &pc);
+            if (s == LBM_OK && (int)pit.size() != b->n_sitems) s = bfail(b, LBM_ERR_ARG, "persistent work list size");
+            if (s == LBM_OK) s = upload(b->off_pitems, pit.data(), pit.size() * sizeof(lbm::StagedItem), "persistent work list");
+            if (s == LBM_OK) s = upload(b->off_pcav, pc.data(), pc.size() * sizeof(lbm::PersistCavity), "persistent layout");
             for (int i = 0; i < 2 && s == LBM_OK; ++i)
                 s = upload(b->off_maps + (size_t)i * n * sizeof(CUtensorMap), b->hmaps[i].data(),
                            (size_t)n * sizeof(CUtensorMap), "tensor maps");
@@ -499,7 +530,22 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t n, int mode) {
     if (!b || n < 0) return b ? bfail(b, LBM_ERR_ARG, "negative step count") : LBM_ERR_ARG;
     if (b->timeout) return bfail(b, LBM_ERR_TIMEOUT, "a bounded wait of the staged step gave up");
     if (b->nonfinite) return bfail(b, LBM_ERR_NONFINITE, "non-finite velocity or temperature");
-    if (mode < LBM_BATCH_FUSED || mode > LBM_BATCH_PER_CASE) return bfail(b, LBM_ERR_ARG, "unknown mode");
+    if (mode < LBM_BATCH_FUSED || mode > LBM_BATCH_PERSISTENT) return bfail(b, LBM_ERR_ARG, "unknown mode");
+    if (mode == LBM_BATCH_PERSISTENT) {
+        if (!b->staged) return bfail(b, LBM_ERR_ARG, "the persistent step needs the staged kernel (FP32, walled cavities)");
+        if (n == 0) return LBM_OK;
+        if (n > (int64_t)1 << 30) return bfail(b, LBM_ERR_ARG, "too many steps for one persistent launch");
+        int* done = b->done();
+        cudaError_t e = lbm::launch_step_batch_persist(
+            (const lbm::BatchCavity<float>*)(b->ws + b->off_cav), b->pcav(), b->maps(0), b->pitems(), b->n_sitems, b->n,
+            (float*)b->buf(0), (float*)b->buf(1), b->cur, (uint32_t)b->steps, (int)n, done, done + b->n_sitems,
+            b->flag(), b->sms, b->stream);
+        if (e != cudaSuccess) return bcuda(b, e, "persistent batched step");
+        b->launches += 1;
+        b->steps += n;
+        if (n & 1) b->cur = 1 - b->cur;
+        return LBM_OK;
+    }
     if (mode == LBM_BATCH_GRAPH && b->stream == nullptr)
         return bfail(b, LBM_ERR_ARG, "graph mode needs a stream other than the legacy default stream");
     int64_t done = 0;

@@ -144,6 +144,23 @@ struct StagedItem {
 cudaError_t launch_step_batch_tma(const BatchCavity<float>* cav, const CUtensorMap* maps, const StagedItem* items,
                                   int n_items, const float* src, float* dst, uint32_t step, cudaStream_t st);
 int tma_batch_rows();
+
+// Layout of one cavity's items in the persistent work list: items first ..
+// first + ns * nb - 1, segment-major (item first + seg * nb + band).
+struct PersistCavity {
+    int first, nb, ns, pad;
+};
+
+// Persistent staged batch step: `nsteps` steps of every cavity in one
+// cooperative launch (one block per SM slot), the items ordered as
+// PersistCavity describes; maps[buffer * n_cav + c] is cavity c's tensor map
+// of buffer `buffer`; done[n_items] and abort_word are scratch of the call
+// (reset on the stream before the launch).  buf0/buf1: the two population
+// buffers, cur: the one that holds the current state.
+cudaError_t launch_step_batch_persist(const BatchCavity<float>* cav, const PersistCavity* pcav, const CUtensorMap* maps,
+                                      const StagedItem* items, int n_items, int n_cav, float* buf0, float* buf1,
+                                      int cur, uint32_t step0, int nsteps, int* done, int* abort_word, int* flag,
+                                      int sms, cudaStream_t st);
 // One wait that must give up (nothing arrives): sets bit 1 of *flag.
 cudaError_t launch_wait_selftest(int* flag, cudaStream_t st);
 

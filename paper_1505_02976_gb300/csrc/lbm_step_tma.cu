@@ -106,18 +106,32 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 
 // The 17 plane rows output row y pulls from, into one slot: plane p from
 // global row y + plane_dy(p), columns x0 - halo .. x0 + 127 + halo.
+// FP16 rows are described to the copy engine as 4-D, (8 columns, columns / 8,
+// rows, planes): a box dimension holds at most 256 elements, and the 272
+// columns of an FP16 band (256 + 2 x 8 halo) become a box of (8, 34, 1, 1),
+// still one contiguous run in shared memory.  The innermost coordinate is
+// always 0 and the column-group coordinate x / 8 may be -1 at the left edge
+// (zero fill, never read).
 template <class S>
 __device__ __forceinline__ void tma_load_slot(const CUtensorMap* tm, S* slot, uint64_t* bar, int x, int y) {
     using L = TmaLayout<S>;
     const uint32_t b = smem_addr(bar);
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(L::bytes) : "memory");
 #pragma unroll
-    for (int p = 0; p < NPLANES; ++p)
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-            "%4}], [%5];" ::"r"(smem_addr(slot + p * L::plane)),
-            "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y + plane_dy(p)), "r"(p), "r"(b)
-            : "memory");
+    for (int p = 0; p < NPLANES; ++p) {
+        if constexpr (sizeof(S) == 2)
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4, %5}], [%6];" ::"r"(smem_addr(slot + p * L::plane)),
+                "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(x >> 3), "r"(y + plane_dy(p)), "r"(p), "r"(b)
+                : "memory");
+        else
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4}], [%5];" ::"r"(smem_addr(slot + p * L::plane)),
+                "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y + plane_dy(p)), "r"(p), "r"(b)
+                : "memory");
+    }
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -167,7 +181,7 @@ __device__ __forceinline__ void staged_setup(unsigned char* smem_raw, S*& stage,
 // (each slot and barrier is used once).
 template <class S>
 __device__ __forceinline__ void staged_issue(const CUtensorMap* tm, S* stage, uint64_t* bar, int x0, int y0, int rows,
-                                             int ny) {
+                                             int ny, uint32_t /*phases*/ = 0u) {
     const int yb = max(y0, 1), ye = min(min(y0 + rows, ny), ny - 1);
     for (int r = yb; r < ye; ++r)
         tma_load_slot(tm, stage + (r - yb) * TmaLayout<S>::slot, bar + (r - yb), x0 - TmaLayout<S>::halo, r);
@@ -178,8 +192,9 @@ __device__ __forceinline__ void staged_issue(const CUtensorMap* tm, S* stage, ui
 // kTRows) of the lattice k with population buffers src / dst.  step: the
 // step number (the stochastic rounding of FP16 stores draws from it).
 template <class S, bool EPS_FIELD, bool TAU1>
-__device__ __forceinline__ void staged_rows(const KConst<float>& k, const S* __restrict__ src, S* __restrict__ dst,
-                                            int x0, int y0, int rows, uint32_t step, const S* stage, uint64_t* bar) {
+__device__ __forceinline__ bool staged_rows(const KConst<float>& k, const S* __restrict__ src, S* __restrict__ dst,
+                                            int x0, int y0, int rows, uint32_t step, const S* stage, uint64_t* bar,
+                                            uint32_t phases = 0u) {
     using L = TmaLayout<S>;
     const int tid = threadIdx.x;
     const int y1 = min(y0 + rows, k.ny);
@@ -205,7 +220,7 @@ __device__ __forceinline__ void staged_rows(const KConst<float>& k, const S* __r
     // all copies have landed before the block can release its shared memory.
     bool ok = true;
     for (int y = yb; y < ye && (active || tid == 0); ++y) {
-        if (!tma_wait(bar + (y - yb), 0u)) {
+        if (!tma_wait(bar + (y - yb), (phases >> (y - yb)) & 1u)) {
             ok = false;
             break;
         }
@@ -238,8 +253,9 @@ __device__ __forceinline__ void staged_rows(const KConst<float>& k, const S* __r
         atomicOr(k.flag, 2);
         // let this block's copies land before its shared memory is released
         if (tid == 0)
-            for (int r = yb; r < ye; ++r) (void)tma_wait(bar + (r - yb), 0u);
+            for (int r = yb; r < ye; ++r) (void)tma_wait(bar + (r - yb), (phases >> (r - yb)) & 1u);
     }
+    return ok;
 }
 
 // The FP16 form of staged_rows: one pair of x-adjacent nodes per thread,
@@ -406,6 +422,124 @@ k_step_batch_tma(const BatchCavity<float>* __restrict__ cav, const CUtensorMap* 
         staged_rows<float, false, false>(ks, src + off, dst + off, w.x0, w.y0, kTRows, step, stage, bar);
 }
 
+// Persistent form of the staged batch step: one cooperative launch runs
+// `nsteps` steps.  Every resident block takes the work items i = blockIdx.x,
+// blockIdx.x + gridDim.x, ... of the list (cavity by cavity, segment-major,
+// so item first + seg * nb + band of a cavity) in the same order at every
+// step.  Before it updates item i at step s it waits until the up to eight
+// neighbouring items of the same cavity (bands and segments +-1) have
+// completed step s - 1 (done[j] >= s): their outputs of step s - 1 are the
+// values item i pulls, and their reads of step s - 1 were of the buffer item
+// i now writes.  A block completes an item by a release of done[i] = s + 1
+// after all its threads' stores; the waiting thread acquires it and fences
+// the async proxy before it issues the tensor copies.  All blocks are
+// co-resident (cooperative launch) and take their items in the same order,
+// so every wait ends: an item of step s needs only items of step s - 1,
+// which their blocks finish before they start step s.  The waits are
+// bounded: one that gives up sets the timeout bit of the flag and the abort
+// word, and every block then leaves.
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0: wait until every neighbour of item (seg, band) of a cavity laid
+// out as pc has done[j] >= need; false if a wait gave up or another block
+// aborted.
+__device__ bool wait_neighbours(const int* done, const PersistCavity& pc, int seg, int band, int need,
+                                int* abort_word) {
+    const unsigned long long t0 = global_ns();
+    long long polls = 0;
+    for (int ds = -1; ds <= 1; ++ds) {
+        const int sg = seg + ds;
+        if (sg < 0 || sg >= pc.ns) continue;
+        for (int db = -1; db <= 1; ++db) {
+            const int bd = band + db;
+            if (bd < 0 || bd >= pc.nb) continue;
+            const int* d = done + pc.first + sg * pc.nb + bd;
+            while (ld_acquire_gpu(d) < need) {
+                if ((++polls & 63) == 0) {
+                    if (*(volatile int*)abort_word) return false;
+                    if (polls > kTWaitPolls || global_ns() - t0 > kTWaitNs) return false;
+                }
+            }
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kTBand, TmaLayout<float>::blocks)
+k_step_batch_persist(const BatchCavity<float>* __restrict__ cav, const PersistCavity* __restrict__ pcav,
+                     const CUtensorMap* __restrict__ maps, const StagedItem* __restrict__ items, int n_items,
+                     int n_cav, float* buf0, float* buf1, int cur, uint32_t step0, int nsteps, int* done,
+                     int* abort_word, int* flag) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ KConst<float> ks;
+    __shared__ long long off;
+    __shared__ int go;
+    float* stage;
+    uint64_t* bar;
+    staged_setup<float>(smem_raw, stage, bar);
+    __syncthreads();  // barriers initialised
+    uint32_t phases = 0u;  // current parity of each slot's barrier
+    int have = -1;         // cavity whose constants are in ks
+    for (int s = 0; s < nsteps; ++s) {
+        const int sb = (cur + s) & 1;
+        const float* src = sb ? buf1 : buf0;
+        float* dst = sb ? buf0 : buf1;
+        for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
+            const StagedItem w = items[i];
+            if (threadIdx.x == 0) {
+                const PersistCavity pc = pcav[w.cavity];
+                const int ok = wait_neighbours(done, pc, w.y0 / kTRows, w.x0 / kTBand, s, abort_word);
+                if (ok) {
+                    // order the acquired generic-proxy writes before the copies
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    staged_issue<float>(maps + (size_t)sb * n_cav + w.cavity, stage, bar, w.x0, w.y0, kTRows, w.ny,
+                                        phases);
+                } else {
+                    atomicOr(flag, 2);
+                    atomicExch(abort_word, 1);
+                }
+                go = ok;
+            }
+            if (w.cavity != have) {
+                const int* from = reinterpret_cast<const int*>(&cav[w.cavity].k);
+                int* to = reinterpret_cast<int*>(&ks);
+                for (int q = threadIdx.x; q < (int)(sizeof(KConst<float>) / sizeof(int)); q += kTBand) to[q] = from[q];
+                if (threadIdx.x == 0) off = cav[w.cavity].offset;
+                have = w.cavity;
+            }
+            __syncthreads();  // go, constants, offset
+            if (!go) return;
+            bool ok;
+            if (ks.omf == 0.f && ks.omT == 0.f)
+                ok = staged_rows<float, false, true>(ks, src + off, dst + off, w.x0, w.y0, kTRows, step0 + s, stage,
+                                                     bar, phases);
+            else
+                ok = staged_rows<float, false, false>(ks, src + off, dst + off, w.x0, w.y0, kTRows, step0 + s, stage,
+                                                      bar, phases);
+            // the stores of this item become visible to the copies of the
+            // blocks that pull from it at the next step
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            const int used = min(min(w.y0 + kTRows, w.ny), w.ny - 1) - max(w.y0, 1);  // slots armed
+            phases ^= used > 0 ? ((1u << used) - 1u) : 0u;
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicExch(abort_word, 1);
+                return;
+            }
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st_release_gpu(done + i, s + 1);
+            }
+        }
+    }
+}
+
 // Self-test of the bounded wait: an mbarrier that nothing arrives on, waited
 // on with a 20 ms limit; the wait gives up and sets the timeout bit of the
 // flag, exactly as a step whose copies never landed would.
@@ -445,13 +579,25 @@ bool make_step_tensor_map(const KConst<float>& k, const S* buf, CUtensorMap* out
             return false;
         encode = reinterpret_cast<Encode>(fn);
     }
-    const cuuint64_t dims[3] = {(cuuint64_t)k.nx, (cuuint64_t)k.ny, (cuuint64_t)NPLANES};
-    const cuuint64_t strides[2] = {(cuuint64_t)k.pitch * sizeof(S), (cuuint64_t)k.plane * sizeof(S)};
-    const cuuint32_t box[3] = {(cuuint32_t)TmaLayout<S>::box, 1u, 1u};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    return encode(out, TmaType<S>::value, 3, const_cast<S*>(buf), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    if constexpr (sizeof(S) == 2) {
+        // (8 columns, column groups, rows, planes); the pitch is a multiple of
+        // 64 columns, so every group of 8 up to nx rounded up lies in the row
+        static_assert(TmaLayout<S>::box % 8 == 0, "FP16 boxes are whole groups of 8 columns");
+        const cuuint64_t dims[4] = {8u, (cuuint64_t)((k.nx + 7) / 8), (cuuint64_t)k.ny, (cuuint64_t)NPLANES};
+        const cuuint64_t strides[3] = {8 * sizeof(S), (cuuint64_t)k.pitch * sizeof(S), (cuuint64_t)k.plane * sizeof(S)};
+        const cuuint32_t box[4] = {8u, (cuuint32_t)(TmaLayout<S>::box / 8), 1u, 1u};
+        return encode(out, TmaType<S>::value, 4, const_cast<S*>(buf), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    } else {
+        const cuuint64_t dims[3] = {(cuuint64_t)k.nx, (cuuint64_t)k.ny, (cuuint64_t)NPLANES};
+        const cuuint64_t strides[2] = {(cuuint64_t)k.pitch * sizeof(S), (cuuint64_t)k.plane * sizeof(S)};
+        const cuuint32_t box[3] = {(cuuint32_t)TmaLayout<S>::box, 1u, 1u};
+        return encode(out, TmaType<S>::value, 3, const_cast<S*>(buf), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
 }
 
 bool tma_step_supported(const KConst<float>& k) {
@@ -525,6 +671,36 @@ cudaError_t launch_step_batch_tma(const BatchCavity<float>* cav, const CUtensorM
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_step_batch_tma, cav, maps, items, src, dst, step);
+}
+
+cudaError_t launch_step_batch_persist(const BatchCavity<float>* cav, const PersistCavity* pcav, const CUtensorMap* maps,
+                                      const StagedItem* items, int n_items, int n_cav, float* buf0, float* buf1,
+                                      int cur, uint32_t step0, int nsteps, int* done, int* abort_word, int* flag,
+                                      int sms, cudaStream_t st) {
+    if (n_items < 1 || nsteps < 1) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_step_batch_persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TmaLayout<float>::smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batch_persist, kTBand, TmaLayout<float>::smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    const int grid = min(n_items, per_sm * sms);
+    e = cudaMemsetAsync(done, 0, (size_t)n_items * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(abort_word, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kTBand);
+    cfg.dynamicSmemBytes = TmaLayout<float>::smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step_batch_persist, cav, pcav, maps, items, n_items, n_cav, buf0, buf1, cur,
+                              step0, nsteps, done, abort_word, flag);
 }
 
 int tma_batch_rows() { return kTRows; }

@@ -34,7 +34,7 @@ EXPORTED = ("lbm_params_default", "lbm_derived", "lbm_workspace_size", "lbm_crea
             "lbm_stream_function", "lbm_set_moment_segments", "lbm_wait_selftest",
             "lbm_set_step_staging", "lbm_step_staged", "lbm_batch_set_staging", "lbm_batch_staged",
             "lbm_check_guards", "lbm_batch_check_guards", "lbm_fp64_peak")
-BATCH_MODE = {"fused": 0, "graph": 1, "per_case": 2}
+BATCH_MODE = {"fused": 0, "graph": 1, "per_case": 2, "persistent": 3}
 
 
 class LbmError(RuntimeError):

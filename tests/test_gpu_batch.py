@@ -172,3 +172,40 @@ def test_staging_is_refused_for_fp64_and_periodic_batches():
     with pytest.raises(lbm.LbmError):
         b.staged = True
     b.close()
+
+
+def test_persistent_batch_matches_the_per_step_launches():
+    """The persistent form (every step of a call in one cooperative launch,
+    items waiting only on their neighbours' previous step) gives the fused
+    staged step's results: bit for bit at tau = 1, to FP32 rounding for the
+    tau != 1 cavity; calls of odd and even length keep the buffer parity; the
+    workspace guards stay intact; a non-staged batch refuses the mode."""
+    probs = _walled_problems()
+    rng = np.random.Generator(np.random.PCG64(23))
+    fields = [W.random_fields(p, seed=int(rng.integers(1 << 30)), amp_u=2e-3, amp_T=0.3) for p in probs]
+    runs = {}
+    for mode in ("fused", "persistent"):
+        b = lbm.Batch(probs, "f32")
+        assert b.staged
+        for c, f in enumerate(fields):
+            b.set_fields(c, *f)
+        for n in (37, 1, 62):
+            b.step(n, mode)
+        b.sync()
+        assert b.steps == 100
+        b.check_guards()
+        runs[mode] = [b.moments(c) for c in range(len(probs))]
+        b.close()
+    for c, p in enumerate(probs):
+        tau1 = p["tau_f"] == 1.0 and p["tau_T"] == 1.0
+        for k in ("ux", "uy", "T", "p"):
+            a, r = runs["persistent"][c][k], runs["fused"][c][k]
+            if tau1:
+                assert np.array_equal(a, r), (c, k)
+            else:
+                assert np.abs(a - r).max() <= 1e-5 * max(np.abs(r).max(), 1e-12), (c, k)
+    b = lbm.Batch(_walled_problems()[:2], "f32")
+    b.staged = False
+    with pytest.raises(lbm.LbmError):
+        b.step(3, "persistent")
+    b.close()
