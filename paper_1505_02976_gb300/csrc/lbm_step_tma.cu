@@ -42,6 +42,9 @@ constexpr int kTBand = 128;  // output columns per band = threads per block
 #define LBM_TMA_ROWS 4
 #endif
 constexpr int kTRows = LBM_TMA_ROWS;  // output rows staged per block (the segment's interior rows)
+#ifndef LBM_ALT_SWEEP
+#define LBM_ALT_SWEEP 1
+#endif
 constexpr unsigned long long kTWaitNs = 2000000000ull;  // a wait gives up after 2 s
 constexpr long long kTWaitPolls = 1ll << 28;             // ... or after this many polls
 
@@ -73,7 +76,7 @@ template <> struct TmaLayoutOf<float> { using type = StageLayout<float, kTBand, 
 // FP16 storage: two x-adjacent nodes per thread (one pair per thread), a
 // band of 256 columns, kHRows rows.
 #ifndef LBM_TMA_ROWS_H
-#define LBM_TMA_ROWS_H 2
+#define LBM_TMA_ROWS_H 4
 #endif
 constexpr int kHRows = LBM_TMA_ROWS_H;
 template <> struct TmaLayoutOf<__half> { using type = StageLayout<__half, 2 * kTBand, kHRows>; };
@@ -81,7 +84,7 @@ template <class S> using TmaLayout = typename TmaLayoutOf<S>::type;
 // Resident blocks per SM the kernels are compiled for (registers: 65536 /
 // (threads x blocks) each): FP16 threads carry two nodes.
 #ifndef LBM_TMA_BLOCKS_H
-#define LBM_TMA_BLOCKS_H 6
+#define LBM_TMA_BLOCKS_H 5
 #endif
 template <class S> struct TmaBlocks { static constexpr int value = TmaLayout<S>::blocks; };
 template <> struct TmaBlocks<__half> {
@@ -376,7 +379,15 @@ k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUte
     uint64_t* bar;
     staged_setup<S>(smem_raw, stage, bar);
     const int by = (int)blockIdx.y, nseg = (int)gridDim.y;
-    const int seg = by == 0 ? 0 : (by == 1 ? nseg - 1 : by - 1);
+    // The two wall-row segments first; then the interior segments bottom-up
+    // on even steps and top-down on odd ones, so that the first blocks of a
+    // step read the rows the previous step wrote last, while they are still
+    // in L2 (the order changes no value: every node depends on the previous
+    // state alone).
+    int seg = by == 0 ? 0 : (by == 1 ? nseg - 1 : by - 1);
+#if LBM_ALT_SWEEP
+    if (step & 1u) seg = by == 0 ? nseg - 1 : (by == 1 ? 0 : nseg - by);
+#endif
     const int x0 = blockIdx.x * TmaLayout<S>::band, y0 = seg * rows;
     __syncthreads();  // barriers initialised (the other threads go on while thread 0 issues)
     // the previous step's writes must be visible before the first copy
