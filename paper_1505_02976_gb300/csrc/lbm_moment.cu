@@ -11,29 +11,37 @@
 // The lattice therefore stores those nine moments (36 bytes per node in
 // FP32 instead of 68) and each step
 //   1. expands the moments of every node (and a one-node halo) into its
-//      17 post-collision populations, in shared memory,
-//   2. pulls the 17 populations of each node from its neighbours there,
+//      17 post-collision populations,
+//   2. pulls the 17 populations of each node from its neighbours,
 //   3. computes the new moments (fast_moments), and the boundary state of the
 //      wall nodes from their x_f, x_ff neighbours, and stores them.
-// A block owns a band of up to 126 columns and a segment of rows; it marches
-// up its rows keeping the expansions of three rows in a shared ring, so every
-// node is expanded once per band it borders (2 halo columns per band, 2 halo
-// rows per segment).
+// Each warp owns a strip of up to 30 columns (32 lanes: the strip and one
+// halo column on each side) and a segment of rows, and marches up the
+// segment: lane L expands its column's node of row y + 1 once, keeps in
+// registers only the values still to be pulled (the six moving up, the five
+// moving along x and staying, the six moving down), and takes its x
+// neighbours' values by warp shuffles (12 per node).  No shared memory and
+// no block barrier: a wall node reads its x_f and x_ff neighbours back from
+// the output after a warp barrier, and they always lie in the same strip
+// (strips are at least 3 columns wide, segments at least 3 rows tall).
+// Every node is expanded once per strip and segment it borders (2 halo
+// columns per 30, 2 halo rows per segment).
 #include <math.h>
+
+#include <algorithm>
 
 #include "lbm_internal.h"
 
+#ifndef LBM_MOMENT_WAVES
+#define LBM_MOMENT_WAVES 1
+#endif
+
 namespace lbm {
 
-constexpr int kMBlock = 128;           // threads = expansion columns of a band
-constexpr int kMBand = kMBlock - 2;    // output columns of a band, at most
-// Expanded rows kept in shared memory: rows y - 1, y, y + 1 while row y is
-// updated, and a barrier after the update frees the slot of row y - 1.  (A
-// fourth slot would save that barrier but costs two resident blocks per SM,
-// which measured slower.)
-constexpr int kMRing = 3;
+constexpr int kMBlock = 128;     // threads per block: four independent warps
+constexpr int kMStrip = 30;      // output columns of a strip, at most (32 lanes with the halo)
 constexpr int kMaxDevices = 64;
-template <class R> struct MomentOccupancy { static constexpr int blocks = 8; };
+template <class R> struct MomentOccupancy { static constexpr int blocks = 5; };
 template <> struct MomentOccupancy<double> { static constexpr int blocks = 2; };
 
 // State of a node from its stored moments; F is recomputed from (u, T) as in
@@ -104,45 +112,75 @@ __device__ __forceinline__ void wall_moments(const KConst<R>& k, R* dst, int x, 
     if (!isfinite(m[MTH] + m[MP])) atomicOr(k.flag, 1);
 }
 
-// Band b of nb (columns [x0, x1)) and segment s of ns (rows [y0, y1)): the
-// columns and rows are split as evenly as integer division allows.
-struct Tile {
-    int x0, x1, y0, y1;
+// Values of an expanded node that later rows pull: moving up (f2, f5, f6,
+// h2, h5, h6; pulled by row y + 1), along x or resting (f1, f3, h0, h1, h3;
+// pulled by row y) and moving down (f4, f7, f8, h4, h7, h8; pulled by row
+// y - 1).
+template <class R>
+struct Expanded {
+    R up[6], hz[5], dn[6];
 };
 
-__device__ __forceinline__ Tile tile_of(int nx, int ny) {
-    Tile t;
-    t.x0 = (int)((long long)blockIdx.x * nx / gridDim.x);
-    t.x1 = (int)((long long)(blockIdx.x + 1) * nx / gridDim.x);
-    t.y0 = (int)((long long)blockIdx.y * ny / gridDim.y);
-    t.y1 = (int)((long long)(blockIdx.y + 1) * ny / gridDim.y);
-    return t;
+// The moments of this lane's expansion node in row r (periodic wrap), or
+// nothing when that row or column does not exist.
+template <class R>
+__device__ __forceinline__ void load_moments(const KConst<R>& k, const R* __restrict__ src, int r, int xe, bool ok,
+                                             R* m) {
+    if (!ok) return;
+    const R* s = src + ((long long)r * k.pitch + xe);
+#pragma unroll
+    for (int q = 0; q < kMPlanes; ++q) m[q] = s[q * k.plane32];
+}
+
+template <class R, bool EPS_FIELD, bool SOURCES>
+__device__ __forceinline__ Expanded<R> expand_node(const KConst<R>& k, const R* m, int xe, int r, bool ok) {
+    Expanded<R> e;
+    if (!ok) return e;
+    R fo[9], ho[9];
+    if constexpr (EPS_FIELD) {
+        KConst<R> kc = k;
+        apply_eps(kc, node_eps(k, xe, r));
+        fast_collide<R, true, SOURCES>(kc, state_from_moments(kc, m, r), nullptr, nullptr, fo, ho);
+    } else {
+        fast_collide<R, true, SOURCES>(k, state_from_moments(k, m, r), nullptr, nullptr, fo, ho);
+    }
+    e.up[0] = fo[2]; e.up[1] = fo[5]; e.up[2] = fo[6];
+    e.up[3] = ho[2]; e.up[4] = ho[5]; e.up[5] = ho[6];
+    e.hz[0] = fo[1]; e.hz[1] = fo[3]; e.hz[2] = ho[0]; e.hz[3] = ho[1]; e.hz[4] = ho[3];
+    e.dn[0] = fo[4]; e.dn[1] = fo[7]; e.dn[2] = fo[8];
+    e.dn[3] = ho[4]; e.dn[4] = ho[7]; e.dn[5] = ho[8];
+    return e;
 }
 
 // One step from the moments in src to the moments in dst.  SOURCES = false:
 // src is the state lbm_set_fields writes, whose populations are the
-// equilibria alone (no F_i, P_i, Q_i).
+// equilibria alone (no F_i, P_i, Q_i).  Warp g of the grid takes strip
+// g % nstrips and segment g / nstrips; strips and segments split the columns
+// and rows as evenly as integer division allows.
 template <class R, bool EPS_FIELD, bool SOURCES>
 __global__ void __launch_bounds__(kMBlock, MomentOccupancy<R>::blocks)
-k_step_m(const __grid_constant__ KConst<R> k, const R* __restrict__ src, R* dst) {
+k_step_m(const __grid_constant__ KConst<R> k, const R* __restrict__ src, R* dst, int nstrips, int nseg) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* ring = reinterpret_cast<R*>(smem_raw);  // [kMRing][17][kMBlock]
-    const int tid = threadIdx.x;
-    const Tile t = tile_of(k.nx, k.ny);
+    const int lane = threadIdx.x & 31;
+    const int g = blockIdx.x * (kMBlock / 32) + (threadIdx.x >> 5);
+    if (g >= nstrips * nseg) return;  // a whole warp leaves together
+    const int strip = g % nstrips, seg = g / nstrips;
+    const int xa = (int)((long long)strip * k.nx / nstrips), xb = (int)((long long)(strip + 1) * k.nx / nstrips);
+    const int y0 = (int)((long long)seg * k.ny / nseg), y1 = (int)((long long)(seg + 1) * k.ny / nseg);
     const bool perx = k.bc[SW] == BC_PERIODIC, pery = k.bc[SS] == BC_PERIODIC;
 
-    // expansion column of this thread: x0 - 1 + tid, needed up to x1
-    int xe = t.x0 - 1 + tid;
-    bool xe_ok = xe <= t.x1;
+    // expansion column of this lane: xa - 1 + lane, needed up to xb
+    int xe = xa - 1 + lane;
+    bool xe_ok = xe <= xb;
     if (xe < 0 || xe >= k.nx) {
         if (perx) xe = xe < 0 ? xe + k.nx : xe - k.nx;
         else xe_ok = false;
     }
-    // output column of this thread
-    const int x = t.x0 - 1 + tid;
-    const bool out_col = tid >= 1 && x < t.x1;
+    // output column of this lane
+    const int x = xa - 1 + lane;
+    const bool out_col = lane >= 1 && x < xb;
+    const bool wall_col = out_col && is_wall_x(k, x);
 
     // row r of the lattice as stored (periodic wrap), or -1 if it does not exist
     auto row_of = [&](int r) {
@@ -150,105 +188,73 @@ k_step_m(const __grid_constant__ KConst<R> k, const R* __restrict__ src, R* dst)
         if (!pery) return -1;
         return r < 0 ? r + k.ny : r - k.ny;
     };
-    // the moments of this thread's expansion node in row r (issued early so
-    // that the loads are in flight while the previous row is processed)
-    auto load_row = [&](int r, R* m) {
-        r = row_of(r);
-        if (r < 0 || !xe_ok) return;
-        const R* s = src + ((long long)r * k.pitch + xe);
-#pragma unroll
-        for (int q = 0; q < kMPlanes; ++q) m[q] = s[q * k.plane32];
-    };
-    auto expand = [&](int r, int slot, const R* m) {
-        r = row_of(r);
-        if (r < 0 || !xe_ok) return;
-        R fo[9], ho[9];
-        if constexpr (EPS_FIELD) {
-            KConst<R> kc = k;
-            apply_eps(kc, node_eps(k, xe, r));
-            fast_collide<R, true, SOURCES>(kc, state_from_moments(kc, m, r), nullptr, nullptr, fo, ho);
-        } else {
-            fast_collide<R, true, SOURCES>(k, state_from_moments(k, m, r), nullptr, nullptr, fo, ho);
-        }
-        R* sl = ring + slot * (NPLANES * kMBlock);
-#pragma unroll
-        for (int i = 1; i < 9; ++i) sl[(i - 1) * kMBlock + tid] = fo[i];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) sl[(8 + i) * kMBlock + tid] = ho[i];
-    };
+    const bool wallS = !pery && y0 == 0;        // this segment holds the S wall row
+    const bool wallN = !pery && y1 == k.ny;     // ... the N wall row
+    const bool wallWE = !perx && (xa == 0 || xb == k.nx);
 
-    // interior node (x, y): pull from the ring (slots of rows y-1, y, y+1)
-    auto update = [&](int y, int sm, int s0, int sp) {
-        const R* rm = ring + sm * (NPLANES * kMBlock);
-        const R* r0 = ring + s0 * (NPLANES * kMBlock);
-        const R* rp = ring + sp * (NPLANES * kMBlock);
+    R mn[kMPlanes];
+    int r = row_of(y0 - 1);
+    load_moments(k, src, r, xe, xe_ok && r >= 0, mn);
+    Expanded<R> em = expand_node<R, EPS_FIELD, SOURCES>(k, mn, xe, r, xe_ok && r >= 0);  // row y - 1
+    r = row_of(y0);
+    load_moments(k, src, r, xe, xe_ok && r >= 0, mn);
+    Expanded<R> e0 = expand_node<R, EPS_FIELD, SOURCES>(k, mn, xe, r, xe_ok && r >= 0);  // row y
+    int rn = row_of(y0 + 1);
+    load_moments(k, src, rn, xe, xe_ok && rn >= 0, mn);  // row y + 1, expanded in the loop
+    for (int y = y0; y < y1; ++y) {
+        R mc[kMPlanes];
+#pragma unroll
+        for (int q = 0; q < kMPlanes; ++q) mc[q] = mn[q];
+        const int rc = rn;
+        rn = row_of(y + 2);
+        if (y + 2 <= y1) load_moments(k, src, rn, xe, xe_ok && rn >= 0, mn);
+        const Expanded<R> ep = expand_node<R, EPS_FIELD, SOURCES>(k, mc, xe, rc, xe_ok && rc >= 0);  // row y + 1
+        // pulls of node (x, y): f_i(x) = f_i*(x - c_i); c: 1 (+1,0) 2 (0,+1)
+        // 3 (-1,0) 4 (0,-1) 5 (+1,+1) 6 (-1,+1) 7 (-1,-1) 8 (+1,-1)
         R f[9], h[9];
-        // f_i(x) = f_i*(x - c_i); c: 1 (+1,0) 2 (0,+1) 3 (-1,0) 4 (0,-1)
-        // 5 (+1,+1) 6 (-1,+1) 7 (-1,-1) 8 (+1,-1)
-        f[1] = r0[0 * kMBlock + tid - 1];
-        f[2] = rm[1 * kMBlock + tid];
-        f[3] = r0[2 * kMBlock + tid + 1];
-        f[4] = rp[3 * kMBlock + tid];
-        f[5] = rm[4 * kMBlock + tid - 1];
-        f[6] = rm[5 * kMBlock + tid + 1];
-        f[7] = rp[6 * kMBlock + tid + 1];
-        f[8] = rp[7 * kMBlock + tid - 1];
-        h[0] = r0[8 * kMBlock + tid];
-        h[1] = r0[9 * kMBlock + tid - 1];
-        h[2] = rm[10 * kMBlock + tid];
-        h[3] = r0[11 * kMBlock + tid + 1];
-        h[4] = rp[12 * kMBlock + tid];
-        h[5] = rm[13 * kMBlock + tid - 1];
-        h[6] = rm[14 * kMBlock + tid + 1];
-        h[7] = rp[15 * kMBlock + tid + 1];
-        h[8] = rp[16 * kMBlock + tid - 1];
-        const long long at = (long long)y * k.pitch + x;
-        if constexpr (EPS_FIELD) {
-            KConst<R> kc = k;
-            apply_eps(kc, node_eps(k, x, y));
-            store_moments(k, dst, at, fast_moments(kc, f, h, y));
-        } else {
-            store_moments(k, dst, at, fast_moments(k, f, h, y));
-        }
-    };
-
-    const bool wallS = !pery && t.y0 == 0;             // this segment holds the S wall row
-    const bool wallN = !pery && t.y1 == k.ny;          // ... the N wall row
-    const bool wallWE = !perx && (t.x0 == 0 || t.x1 == k.nx);
-    int sm = 0, s0 = 1, sp = 2;
-    R mnext[kMPlanes];
-    load_row(t.y0 - 1, mnext);
-    expand(t.y0 - 1, sm, mnext);
-    load_row(t.y0, mnext);
-    expand(t.y0, s0, mnext);
-    load_row(t.y0 + 1, mnext);
-    for (int y = t.y0; y < t.y1; ++y) {
-        R mcur[kMPlanes];
-#pragma unroll
-        for (int q = 0; q < kMPlanes; ++q) mcur[q] = mnext[q];
-        if (y + 2 <= t.y1) load_row(y + 2, mnext);
-        expand(y + 1, sp, mcur);
-        __syncthreads();
+        f[1] = __shfl_up_sync(0xffffffffu, e0.hz[0], 1);
+        f[2] = em.up[0];
+        f[3] = __shfl_down_sync(0xffffffffu, e0.hz[1], 1);
+        f[4] = ep.dn[0];
+        f[5] = __shfl_up_sync(0xffffffffu, em.up[1], 1);
+        f[6] = __shfl_down_sync(0xffffffffu, em.up[2], 1);
+        f[7] = __shfl_down_sync(0xffffffffu, ep.dn[1], 1);
+        f[8] = __shfl_up_sync(0xffffffffu, ep.dn[2], 1);
+        h[0] = e0.hz[2];
+        h[1] = __shfl_up_sync(0xffffffffu, e0.hz[3], 1);
+        h[2] = em.up[3];
+        h[3] = __shfl_down_sync(0xffffffffu, e0.hz[4], 1);
+        h[4] = ep.dn[3];
+        h[5] = __shfl_up_sync(0xffffffffu, em.up[4], 1);
+        h[6] = __shfl_down_sync(0xffffffffu, em.up[5], 1);
+        h[7] = __shfl_down_sync(0xffffffffu, ep.dn[4], 1);
+        h[8] = __shfl_up_sync(0xffffffffu, ep.dn[5], 1);
         const bool wall_row = (wallS && y == 0) || (wallN && y == k.ny - 1);
         if (!wall_row) {
-            if (out_col && !is_wall_x(k, x)) update(y, sm, s0, sp);
+            if (out_col && !wall_col) {
+                const long long at = (long long)y * k.pitch + x;
+                if constexpr (EPS_FIELD) {
+                    KConst<R> kc = k;
+                    apply_eps(kc, node_eps(k, x, y));
+                    store_moments(k, dst, at, fast_moments(kc, f, h, y));
+                } else {
+                    store_moments(k, dst, at, fast_moments(k, f, h, y));
+                }
+            }
             if (wallWE) {
-                __syncthreads();  // x_f, x_ff of the W/E wall nodes are in this row
-                if (out_col && is_wall_x(k, x)) wall_moments(k, dst, x, y);
+                __syncwarp();  // x_f, x_ff of the W/E wall nodes are in this row, in this strip
+                if (wall_col) wall_moments(k, dst, x, y);
             }
         } else if (y == k.ny - 1) {
-            __syncthreads();  // rows ny-2, ny-3 are complete
+            __syncwarp();  // rows ny-2, ny-3 of this strip are complete
             if (out_col) wall_moments(k, dst, x, y);
         }
         if (wallS && y == 2) {
-            __syncthreads();  // rows 1 and 2 are complete: the S wall row
+            __syncwarp();  // rows 1 and 2 of this strip are complete: the S wall row
             if (out_col) wall_moments(k, dst, x, 0);
         }
-        __syncthreads();  // the ring slot of row y - 1 is free
-        const int tmp = sm;
-        sm = s0;
-        s0 = sp;
-        sp = tmp;
+        em = e0;
+        e0 = ep;
     }
 }
 
@@ -295,76 +301,56 @@ __global__ void k_init_m(const __grid_constant__ KConst<R> k, R* __restrict__ ds
 
 // ------------------------------------------------------------------ launchers
 
+// Strips of at most kMStrip columns (split evenly; at least 3 columns each
+// for nx >= 4) and `segments` segments of at least 3 rows.
 template <class R>
-size_t moment_smem_bytes() {
-    return (size_t)kMRing * NPLANES * kMBlock * sizeof(R);
-}
-
-// The ring exceeds the default 48 KB of dynamic shared memory in FP64.
-template <class R, bool E, bool S>
-cudaError_t allow_smem() {
-    // once per device (the attribute belongs to the function on the current device)
-    static bool done[kMaxDevices] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < kMaxDevices && done[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_step_m<R, E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)moment_smem_bytes<R>());
-    if (e == cudaSuccess && dev < kMaxDevices) done[dev] = true;
-    return e;
+void moment_shape(const KConst<R>& k, int segments, int* nstrips, int* nseg) {
+    *nstrips = (k.nx + kMStrip - 1) / kMStrip;
+    int ns = segments > 0 ? segments : 1;
+    if (ns > k.ny / 3) ns = k.ny / 3 > 0 ? k.ny / 3 : 1;
+    *nseg = ns;
 }
 
 template <class R, bool E, bool S>
-cudaError_t launch_m(const KConst<R>& k, const R* src, R* dst, dim3 grid, cudaStream_t st) {
-    const size_t smem = moment_smem_bytes<R>();
-    cudaError_t e = allow_smem<R, E, S>();
-    if (e != cudaSuccess) return e;
+cudaError_t launch_m(const KConst<R>& k, const R* src, R* dst, int nstrips, int nseg, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
+    const long long warps = (long long)nstrips * nseg;
+    cfg.gridDim = dim3((unsigned)((warps + kMBlock / 32 - 1) / (kMBlock / 32)));
     cfg.blockDim = dim3(kMBlock);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_step_m<R, E, S>, k, src, dst);
-}
-
-template <class R>
-dim3 moment_grid(const KConst<R>& k, int segments) {
-    const int nb = (k.nx + kMBand - 1) / kMBand;
-    int ns = segments > 0 ? segments : 1;
-    if (ns > k.ny / 3) ns = k.ny / 3 > 0 ? k.ny / 3 : 1;  // segments keep >= 3 rows
-    return dim3((unsigned)nb, (unsigned)ns);
+    return cudaLaunchKernelEx(&cfg, k_step_m<R, E, S>, k, src, dst, nstrips, nseg);
 }
 
 template <class R>
 int moment_segments_default(const KConst<R>& k) {
-    // about three waves of resident blocks (measured at 2048^2: one wave of
-    // long segments 45.9 GLUPS, three waves 48.3, six 46.2), rows per
-    // segment >= 3 (moment_grid clamps)
+    // about one wave of resident warps (segments of >= 3 rows; moment_shape clamps)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 0;
-    if (allow_smem<R, false, true>() == cudaSuccess)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_m<R, false, true>, kMBlock,
-                                                      moment_smem_bytes<R>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_m<R, false, true>, kMBlock, 0);
     if (per_sm < 1) per_sm = 1;
-    const int nb = (k.nx + kMBand - 1) / kMBand;
-    int ns = 3 * (sms * per_sm) / nb;
-    return ns < 1 ? 1 : ns;
+    const int nstrips = (k.nx + kMStrip - 1) / kMStrip;
+    const long long warps = (long long)sms * per_sm * (kMBlock / 32);
+    const long long ns = (LBM_MOMENT_WAVES * warps) / nstrips;
+    return ns < 1 ? 1 : (int)std::min<long long>(ns, 1 << 20);
 }
 
 template <class R>
 cudaError_t launch_step_m(const KConst<R>& k, const R* src, R* dst, bool sources, int segments, cudaStream_t st) {
-    const dim3 grid = moment_grid(k, segments);
+    int nstrips = 0, nseg = 0;
+    moment_shape(k, segments, &nstrips, &nseg);
     if (k.eps_field)
-        return sources ? launch_m<R, true, true>(k, src, dst, grid, st) : launch_m<R, true, false>(k, src, dst, grid, st);
-    return sources ? launch_m<R, false, true>(k, src, dst, grid, st) : launch_m<R, false, false>(k, src, dst, grid, st);
+        return sources ? launch_m<R, true, true>(k, src, dst, nstrips, nseg, st)
+                       : launch_m<R, true, false>(k, src, dst, nstrips, nseg, st);
+    return sources ? launch_m<R, false, true>(k, src, dst, nstrips, nseg, st)
+                   : launch_m<R, false, false>(k, src, dst, nstrips, nseg, st);
 }
 
 template <class R>
