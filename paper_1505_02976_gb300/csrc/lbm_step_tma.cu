@@ -64,7 +64,7 @@ struct StageLayout {
     static constexpr int slot = NPLANES * plane;                            // elements per slot
     static constexpr unsigned bytes = (unsigned)(NPLANES * box * sizeof(S));  // bytes landing per slot
     // slots, barriers, and room to round the first slot up to 128 bytes
-    static constexpr size_t smem = 128 + (size_t)ROWS * slot * sizeof(S) + 2 * ROWS * sizeof(uint64_t);
+    static constexpr size_t smem = 128 + (size_t)ROWS * slot * sizeof(S) + ROWS * sizeof(uint64_t);
     // resident blocks per SM that the shared memory allows (228 KB per SM,
     // 1 KB reserved per block), at most 8
     static constexpr int blocks = (int)((228 * 1024) / (smem + 1024)) < 8 ? (int)((228 * 1024) / (smem + 1024)) : 8;
@@ -79,23 +79,7 @@ template <> struct TmaLayoutOf<float> { using type = StageLayout<float, kTBand, 
 #define LBM_TMA_ROWS_H 4
 #endif
 constexpr int kHRows = LBM_TMA_ROWS_H;
-// FP16 ring form (LBM_H_RING = 1): a block streams a segment of kHSeg rows
-// through kHSlots row slots; thread 0 refills a slot as soon as every thread
-// has finished the row it held.
-#ifndef LBM_H_RING
-#define LBM_H_RING 0
-#endif
-#ifndef LBM_H_SLOTS
-#define LBM_H_SLOTS 3
-#endif
-#ifndef LBM_H_SEG
-#define LBM_H_SEG 16
-#endif
-constexpr int kHSlots = LBM_H_SLOTS;
-constexpr int kHSeg = LBM_H_SEG;
-template <> struct TmaLayoutOf<__half> {
-    using type = StageLayout<__half, 2 * kTBand, LBM_H_RING ? kHSlots : kHRows>;
-};
+template <> struct TmaLayoutOf<__half> { using type = StageLayout<__half, 2 * kTBand, kHRows>; };
 template <class S> using TmaLayout = typename TmaLayoutOf<S>::type;
 // Resident blocks per SM the kernels are compiled for (registers: 65536 /
 // (threads x blocks) each): FP16 threads carry two nodes.
@@ -381,159 +365,6 @@ __device__ __forceinline__ void staged_rows_pair(const KConst<float>& k, const _
     }
 }
 
-// The FP16 ring form of staged_rows_pair: the segment's interior rows stream
-// through kHSlots slots.  full[s] completes when a slot's copies have landed
-// (count 1 plus the bytes); empty[s] when all kTBand threads have finished
-// the row it held (count kTBand).  Thread 0 issues the first kHSlots rows at
-// the start and each later row into the slot of the row kHSlots before it,
-// once that slot's empty barrier has completed.  Every wait is bounded.
-template <bool EPS_FIELD, bool TAU1>
-__device__ __forceinline__ void staged_rows_pair_ring(const KConst<float>& k, const CUtensorMap* tm,
-                                                      const __half* __restrict__ src, __half* __restrict__ dst,
-                                                      int x0, int y0, int rows, uint32_t step, __half* stage,
-                                                      uint64_t* full, uint64_t* empty) {
-    using L = TmaLayout<__half>;
-    const int tid = threadIdx.x;
-    const int y1 = min(y0 + rows, k.ny);
-    const int yb = max(y0, 1), ye = min(y1, k.ny - 1);  // interior rows of the segment
-    const int nrow = ye - yb;
-    if (tid == 0)
-        for (int i = 0; i < kHSlots && i < nrow; ++i)
-            tma_load_slot(tm, stage + i * L::slot, full + i, x0 - L::halo, yb + i);
-    const int xa = x0 + 2 * tid;
-    // wall nodes of the segment while the first copies fly
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        if (xa + q < k.nx) {
-            if (y0 == 0) wall_update(k, src, dst, xa + q, 0, step);
-            if (y1 == k.ny) wall_update(k, src, dst, xa + q, k.ny - 1, step);
-        }
-    }
-    if (x0 == 0)
-        for (int y = yb + tid; y < ye; y += kTBand) wall_update(k, src, dst, 0, y, step);
-    if (x0 <= k.nx - 1 && k.nx - 1 < x0 + L::band)
-        for (int y = yb + tid; y < ye; y += kTBand) wall_update(k, src, dst, k.nx - 1, y, step);
-    const bool act0 = xa >= 1 && xa <= k.nx - 2;
-    const bool act1 = xa + 1 <= k.nx - 2;
-    const int c = 2 * tid + L::halo;
-    const float out_scale = TAU1 ? 1.0f : k.inv_scale;
-    bool ok = true;
-    int issued = min(kHSlots, nrow);  // rows issued so far (thread 0's count)
-    for (int i = 0; i < nrow; ++i) {
-        const int sl_i = i % kHSlots;
-        const uint32_t par = (uint32_t)(i / kHSlots) & 1u;
-        if (!tma_wait(full + sl_i, par)) {
-            ok = false;
-            break;
-        }
-        const int y = yb + i;
-        if (act0 || act1) {
-            const __half* sl = stage + sl_i * L::slot + c;
-            __half2 pk[NPLANES];
-#pragma unroll
-            for (int p = 0; p < NPLANES; ++p) {
-                const __half* q = sl + p * L::plane;
-                if (plane_dx(p) == 0) {
-                    pk[p] = *reinterpret_cast<const __half2*>(q);
-                } else if (plane_dx(p) < 0) {
-                    const __half2 w0 = *reinterpret_cast<const __half2*>(q - 2);
-                    const __half2 w1 = *reinterpret_cast<const __half2*>(q);
-                    pk[p] = __halves2half2(__high2half(w0), __low2half(w1));
-                } else {
-                    const __half2 w0 = *reinterpret_cast<const __half2*>(q);
-                    const __half2 w1 = *reinterpret_cast<const __half2*>(q + 2);
-                    pk[p] = __halves2half2(__high2half(w0), __low2half(w1));
-                }
-            }
-            // the slot's values are in registers: release it before computing
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(empty + sl_i)) : "memory");
-            float fo[2][9], ho[2][9];
-#pragma unroll
-            for (int n = 0; n < 2; ++n) {
-                if (!(n == 0 ? act0 : act1)) continue;
-                float f[9], h[9];
-#pragma unroll
-                for (int j = 1; j < 9; ++j) f[j] = (n == 0 ? __low2float(pk[j - 1]) : __high2float(pk[j - 1])) * k.scale;
-#pragma unroll
-                for (int j = 0; j < 9; ++j) h[j] = (n == 0 ? __low2float(pk[8 + j]) : __high2float(pk[8 + j])) * k.scale;
-                auto collide = [&](const KConst<float>& kk) {
-                    const FastState<float> st = fast_moments(kk, f, h, y);
-                    if constexpr (TAU1) fast_collide<float, true>(kk, st, f, h, fo[n], ho[n], kk.inv_scale);
-                    else fast_collide<float, false>(kk, st, f, h, fo[n], ho[n]);
-                };
-                if constexpr (EPS_FIELD) {
-                    KConst<float> kc = k;
-                    apply_eps(kc, node_eps(k, xa + n, y));
-                    collide(kc);
-                } else {
-                    collide(k);
-                }
-            }
-            const int at = y * k.pitch + xa;
-            if (act0 && act1) {
-                const Dither dither((uint32_t)at, step);
-                store_pair_half<float>(dst + at, k.plane32, fo[0], ho[0], fo[1], ho[1], out_scale, dither);
-            } else {
-                if (act0) {
-                    Dither d0((uint32_t)at, step);
-                    store_planes_half<float>(dst + at, k.plane32, fo[0], ho[0], out_scale, &d0);
-                }
-                if (act1) {
-                    Dither d1((uint32_t)(at + 1), step);
-                    store_planes_half<float>(dst + at + 1, k.plane32, fo[1], ho[1], out_scale, &d1);
-                }
-            }
-        } else {
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(empty + sl_i)) : "memory");
-        }
-        // thread 0 refills the slot once every thread has released it
-        if (tid == 0 && issued < nrow && issued == i + kHSlots) {
-            if (!tma_wait(empty + sl_i, par)) {
-                ok = false;
-                break;
-            }
-            tma_load_slot(tm, stage + sl_i * L::slot, full + sl_i, x0 - L::halo, yb + issued);
-            ++issued;
-        }
-    }
-    if (!ok) {
-        atomicOr(k.flag, 2);
-        // let every issued copy land before the block releases its shared memory
-        if (tid == 0)
-            for (int r = 0; r < issued; ++r)
-                (void)tma_wait(full + (r % kHSlots), (uint32_t)(r / kHSlots) & 1u);
-    }
-}
-
-template <bool EPS_FIELD, bool TAU1>
-__global__ void __launch_bounds__(kTBand, TmaBlocks<__half>::value)
-k_step_tma_ring(const __grid_constant__ KConst<float> k, const __grid_constant__ CUtensorMap tm,
-                const __half* __restrict__ src, __half* __restrict__ dst, int rows, uint32_t step) {
-    using L = TmaLayout<__half>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
-    __half* stage = reinterpret_cast<__half*>(base);
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)kHSlots * L::slot * sizeof(__half));
-    uint64_t* empty = full + kHSlots;
-    if (threadIdx.x == 0) {
-        for (int s2 = 0; s2 < kHSlots; ++s2) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(full + s2)) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(empty + s2)), "r"(kTBand) : "memory");
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    const int by = (int)blockIdx.y, nseg = (int)gridDim.y;
-    int seg = by == 0 ? 0 : (by == 1 ? nseg - 1 : by - 1);
-#if LBM_ALT_SWEEP
-    if (step & 1u) seg = by == 0 ? nseg - 1 : (by == 1 ? 0 : nseg - by);
-#endif
-    const int x0 = blockIdx.x * L::band, y0 = seg * rows;
-    __syncthreads();  // barriers initialised
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    staged_rows_pair_ring<EPS_FIELD, TAU1>(k, &tm, src, dst, x0, y0, rows, step, stage, full, empty);
-}
-
 // The staged step of one lattice: block (bx, by) owns band bx and a segment
 // of `rows` rows.  The two segments holding the S and N wall rows (a full row
 // of out-of-line wall updates each) are taken by the first two block rows,
@@ -627,28 +458,36 @@ __device__ __forceinline__ void st_release_gpu(int* p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Thread 0: wait until every neighbour of item (seg, band) of a cavity laid
-// out as pc has done[j] >= need; false if a wait gave up or another block
-// aborted.
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Warp 0: wait until every neighbour of item (seg, band) of a cavity laid
+// out as pc has done[j] >= need.  Lane j < 9 polls neighbour (seg + j / 3 - 1,
+// band + j % 3 - 1) with relaxed loads, all nine in flight together; once
+// every lane sees its counter, each takes an acquire fence and the warp
+// synchronises, which orders the neighbours' released stores before
+// everything thread 0 does next.  False if a wait gave up or another block
+// aborted (the same answer in every lane).
 __device__ bool wait_neighbours(const int* done, const PersistCavity& pc, int seg, int band, int need,
                                 int* abort_word) {
+    const int lane = threadIdx.x & 31;
+    const int sg = seg + lane / 3 - 1, bd = band + lane % 3 - 1;
+    const bool mine = lane < 9 && sg >= 0 && sg < pc.ns && bd >= 0 && bd < pc.nb;
+    const int* d = done + pc.first + (mine ? sg * pc.nb + bd : 0);
     const unsigned long long t0 = global_ns();
-    long long polls = 0;
-    for (int ds = -1; ds <= 1; ++ds) {
-        const int sg = seg + ds;
-        if (sg < 0 || sg >= pc.ns) continue;
-        for (int db = -1; db <= 1; ++db) {
-            const int bd = band + db;
-            if (bd < 0 || bd >= pc.nb) continue;
-            const int* d = done + pc.first + sg * pc.nb + bd;
-            while (ld_acquire_gpu(d) < need) {
-                if ((++polls & 63) == 0) {
-                    if (*(volatile int*)abort_word) return false;
-                    if (polls > kTWaitPolls || global_ns() - t0 > kTWaitNs) return false;
-                }
-            }
+    for (long long polls = 0;; ++polls) {
+        const bool seen = !mine || ld_relaxed_gpu(d) >= need;
+        if (__all_sync(0xffffffffu, seen)) break;
+        if ((polls & 63) == 63) {
+            const bool stop = *(volatile int*)abort_word != 0 || polls > kTWaitPolls || global_ns() - t0 > kTWaitNs;
+            if (__any_sync(0xffffffffu, stop)) return false;
         }
     }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    __syncwarp();
     return true;
 }
 
@@ -673,19 +512,21 @@ k_step_batch_persist(const BatchCavity<float>* __restrict__ cav, const PersistCa
         float* dst = sb ? buf0 : buf1;
         for (int i = blockIdx.x; i < n_items; i += gridDim.x) {
             const StagedItem w = items[i];
-            if (threadIdx.x == 0) {
+            if (threadIdx.x < 32) {
                 const PersistCavity pc = pcav[w.cavity];
-                const int ok = wait_neighbours(done, pc, w.y0 / kTRows, w.x0 / kTBand, s, abort_word);
-                if (ok) {
-                    // order the acquired generic-proxy writes before the copies
-                    asm volatile("fence.proxy.async.global;" ::: "memory");
-                    staged_issue<float>(maps + (size_t)sb * n_cav + w.cavity, stage, bar, w.x0, w.y0, kTRows, w.ny,
-                                        phases);
-                } else {
-                    atomicOr(flag, 2);
-                    atomicExch(abort_word, 1);
+                const bool ok = wait_neighbours(done, pc, w.y0 / kTRows, w.x0 / kTBand, s, abort_word);
+                if (threadIdx.x == 0) {
+                    if (ok) {
+                        // order the acquired generic-proxy writes before the copies
+                        asm volatile("fence.proxy.async.global;" ::: "memory");
+                        staged_issue<float>(maps + (size_t)sb * n_cav + w.cavity, stage, bar, w.x0, w.y0, kTRows,
+                                            w.ny, phases);
+                    } else {
+                        atomicOr(flag, 2);
+                        atomicExch(abort_word, 1);
+                    }
+                    go = ok;
                 }
-                go = ok;
             }
             if (w.cavity != have) {
                 const int* from = reinterpret_cast<const int*>(&cav[w.cavity].k);
@@ -808,16 +649,9 @@ static cudaError_t allow_tma_smem() {
 template <class S, bool E, bool T>
 static cudaError_t launch_tma(const cudaLaunchConfig_t& cfg, const KConst<float>& k, const CUtensorMap& tm,
                               const S* src, S* dst, int rows, uint32_t step) {
-    if constexpr (std::is_same<S, __half>::value && LBM_H_RING) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_tma_ring<E, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)TmaLayout<S>::smem);
-        if (e != cudaSuccess) return e;
-        return cudaLaunchKernelEx(&cfg, k_step_tma_ring<E, T>, k, tm, src, dst, rows, step);
-    } else {
-        cudaError_t e = allow_tma_smem<S, E, T>();
-        if (e != cudaSuccess) return e;
-        return cudaLaunchKernelEx(&cfg, k_step_tma<S, E, T>, k, tm, src, dst, rows, step);
-    }
+    cudaError_t e = allow_tma_smem<S, E, T>();
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, k_step_tma<S, E, T>, k, tm, src, dst, rows, step);
 }
 
 template <class S>
@@ -825,7 +659,6 @@ cudaError_t launch_step_tma(const KConst<float>& k, const CUtensorMap& tm, const
                             uint32_t step, cudaStream_t st) {
     if (rows < 1) return cudaErrorInvalidValue;
     if (rows > TmaLayout<S>::rows) rows = TmaLayout<S>::rows;
-    if constexpr (std::is_same<S, __half>::value && LBM_H_RING) rows = kHSeg;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((k.nx + TmaLayout<S>::band - 1) / TmaLayout<S>::band),
                        (unsigned)((k.ny + rows - 1) / rows));
