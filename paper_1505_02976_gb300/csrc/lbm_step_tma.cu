@@ -320,19 +320,49 @@ __device__ __forceinline__ void staged_rows_pair(const KConst<float>& k, const _
                 pk[p] = __halves2half2(__high2half(w0), __low2half(w1));
             }
         }
+        const int at = y * k.pitch + xa;
+        if constexpr (TAU1 && !EPS_FIELD) {
+            if (act0 && act1) {
+                // both nodes interior: the lane form on the pair, node a in
+                // .x and node b in .y of every packed value
+                float2 f2[9], h2[9], fo2[9], ho2[9];
+                const float2 sc = make_float2(k.scale, k.scale);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) f2[i] = __fmul2_rn(__half22float2(pk[i - 1]), sc);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) h2[i] = __fmul2_rn(__half22float2(pk[8 + i]), sc);
+                const LaneState<float2> st = lane_moments<float2>(k, f2, h2, y);
+                lane_collide<float2>(k, st, fo2, ho2, k.inv_scale);
+                const Dither dither((uint32_t)at, step);
+                uint32_t* wd = reinterpret_cast<uint32_t*>(dst + at);
+                const int pw = k.plane32 >> 1;
+#pragma unroll
+                for (int i = 1; i < 9; ++i) wd[(i - 1) * pw] = half2_sr(fo2[i].y, fo2[i].x, dither.word(i - 1));
+#pragma unroll
+                for (int i = 0; i < 9; ++i) wd[(8 + i) * pw] = half2_sr(ho2[i].y, ho2[i].x, dither.word(8 + i));
+                continue;
+            }
+        }
         float fo[2][9], ho[2][9];
 #pragma unroll
         for (int n = 0; n < 2; ++n) {
             if (!(n == 0 ? act0 : act1)) continue;
             float f[9], h[9];
 #pragma unroll
-            for (int i = 1; i < 9; ++i) f[i] = (n == 0 ? __low2float(pk[i - 1]) : __high2float(pk[i - 1])) * k.scale;
+            for (int i = 1; i < 9; ++i)
+                f[i] = __fmul_rn(n == 0 ? __low2float(pk[i - 1]) : __high2float(pk[i - 1]), k.scale);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) h[i] = (n == 0 ? __low2float(pk[8 + i]) : __high2float(pk[8 + i])) * k.scale;
+            for (int i = 0; i < 9; ++i)
+                h[i] = __fmul_rn(n == 0 ? __low2float(pk[8 + i]) : __high2float(pk[8 + i]), k.scale);
             auto collide = [&](const KConst<float>& kk) {
-                const FastState<float> st = fast_moments(kk, f, h, y);
-                if constexpr (TAU1) fast_collide<float, true>(kk, st, f, h, fo[n], ho[n], kk.inv_scale);
-                else fast_collide<float, false>(kk, st, f, h, fo[n], ho[n]);
+                if constexpr (TAU1) {
+                    // the lane form, as the global-load kernel runs it
+                    const LaneState<float> st = lane_moments<float>(kk, f, h, y);
+                    lane_collide<float>(kk, st, fo[n], ho[n], kk.inv_scale);
+                } else {
+                    const FastState<float> st = fast_moments(kk, f, h, y);
+                    fast_collide<float, false>(kk, st, f, h, fo[n], ho[n]);
+                }
             };
             if constexpr (EPS_FIELD) {
                 KConst<float> kc = k;
@@ -342,7 +372,6 @@ __device__ __forceinline__ void staged_rows_pair(const KConst<float>& k, const _
                 collide(k);
             }
         }
-        const int at = y * k.pitch + xa;
         if (act0 && act1) {
             const Dither dither((uint32_t)at, step);
             store_pair_half<float>(dst + at, k.plane32, fo[0], ho[0], fo[1], ho[1], out_scale, dither);
