@@ -108,7 +108,7 @@ template <class S, class R>
 __device__ __forceinline__ R load_pop(const S* p, float) { return R(*p); }
 template <>
 __device__ __forceinline__ float load_pop<__half, float>(const __half* p, float scale) {
-    return __fmul_rn(__half2float(*p), scale);
+    return __half2float(*p) * scale;
 }
 template <class S, class R>
 __device__ __forceinline__ void store_pop(S* p, R v, float) { *p = S(v); }
@@ -691,12 +691,6 @@ __device__ __forceinline__ void fast_collide(const KConst<R>& k, const FastState
     ho[0] = TAU1 ? wscale * c0 : k.omT * h[0] + c0;
 }
 
-}  // namespace lbm
-
-#include "lbm_pair.cuh"
-
-namespace lbm {
-
 // Interior node of one step, fast path.  Same arithmetic as node_moments +
 // eq_terms + BGK collision, rearranged for the GPU: the nine pull sources are
 // 32-bit offsets from the node (periodic wrap by per-thread deltas), plane
@@ -720,18 +714,11 @@ __device__ __forceinline__ void interior_update(const KConst<R>& k, const S* __r
     for (int i = 1; i < 9; ++i) f[i] = load_pop<S, R>(c + ((i - 1) * pl + o[i]), sc);
 #pragma unroll
     for (int i = 0; i < 9; ++i) h[i] = load_pop<S, R>(c + ((8 + i) * pl + o[i]), sc);
+    const FastState<R> s = fast_moments(k, f, h, y);
     R fo[9], ho[9];
     constexpr bool prescale = TAU1 && std::is_same<S, __half>::value;
-    if constexpr (prescale) {
-        // FP16 storage at tau = 1: the lane form, which the staged kernel
-        // also runs (on node pairs), so both store the same bits
-        const LaneState<float> s = lane_moments<float>(k, f, h, y);
-        lane_collide<float>(k, s, fo, ho, k.inv_scale);
-    } else {
-        const FastState<R> s = fast_moments(k, f, h, y);
-        if constexpr (TAU1) fast_collide<R, true>(k, s, f, h, fo, ho);
-        else fast_collide<R, false>(k, s, f, h, fo, ho);
-    }
+    if constexpr (TAU1) fast_collide<R, true>(k, s, f, h, fo, ho, prescale ? R(k.inv_scale) : R(1));
+    else fast_collide<R, false>(k, s, f, h, fo, ho);
     Dither dither((uint32_t)at, step);
     store_planes<S, R>(dst + at, pl, fo, ho, prescale ? 1.0f : k.inv_scale, &dither);
 }

@@ -6,11 +6,12 @@
 // Same moments, quadratic solve, force, pressure, shear rate, temperature
 // gradient and collision as fast_moments / fast_collide (lbm_device.cuh,
 // Secs. 3.1-3.3, Eqs. EQFIN-Eq:Tforce), with every arithmetic operation
-// spelled out (add, multiply, fused multiply-add): each lane of a packed
-// operation rounds exactly as the scalar operation does, so a node updated
-// alone and the same node updated as one half of a pair get the same bits.
-// Used by the FP16-storage steps (both the staged kernel, which updates node
-// pairs, and the global-load kernel, which updates single nodes).
+// spelled out (add, multiply, fused multiply-add).  Each packed operation
+// rounds per lane as the scalar one does, but the compiler may fuse a packed
+// multiply into the add or subtraction that consumes it (one rounding where
+// the scalar code has two), so the results agree with fast_moments /
+// fast_collide to FP32 rounding, not bit for bit.  Used by the FP16-storage
+// staged step on its pairs of interior nodes.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -20,15 +21,35 @@ namespace lbm {
 // ---------------------------------------------------------------- lane ops
 __device__ __forceinline__ float lbc(float, float c) { return c; }
 __device__ __forceinline__ float2 lbc(float2, float c) { return make_float2(c, c); }
+// The packed operations are PTX with round-to-nearest and flush-to-zero
+// (the scalar arithmetic of this build runs with -ftz=true).
+__device__ __forceinline__ unsigned long long lbits(float2 a) { return *reinterpret_cast<unsigned long long*>(&a); }
+__device__ __forceinline__ float2 lfrom(unsigned long long u) { return *reinterpret_cast<float2*>(&u); }
 __device__ __forceinline__ float ladd(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ float2 ladd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 ladd(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(lbits(a)), "l"(lbits(b)));
+    return lfrom(r);
+}
 __device__ __forceinline__ float lsub(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ float2 lsub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 lsub(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(lbits(a)), "l"(lbits(b)));
+    return lfrom(r);
+}
 __device__ __forceinline__ float lmul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float2 lmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 lmul(float2 a, float2 b) {
+    unsigned long long r;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r) : "l"(lbits(a)), "l"(lbits(b)));
+    return lfrom(r);
+}
 // a * b + c, one rounding
 __device__ __forceinline__ float lfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ float2 lfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lfma(float2 a, float2 b, float2 c) {
+    unsigned long long r;
+    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(lbits(a)), "l"(lbits(b)), "l"(lbits(c)));
+    return lfrom(r);
+}
 __device__ __forceinline__ float lsqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ float2 lsqrt(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
 __device__ __forceinline__ float lrcp(float a) { return 1.0f / a; }

@@ -33,6 +33,7 @@
 #include <type_traits>
 
 #include "lbm_internal.h"
+#include "lbm_pair.cuh"
 #include "lbm_step.cuh"
 
 namespace lbm {
@@ -324,13 +325,17 @@ __device__ __forceinline__ void staged_rows_pair(const KConst<float>& k, const _
         if constexpr (TAU1 && !EPS_FIELD) {
             if (act0 && act1) {
                 // both nodes interior: the lane form on the pair, node a in
-                // .x and node b in .y of every packed value
+                // .x and node b in .y of every packed value (the compiler
+                // may fuse some of its multiplies into the following adds,
+                // so the pair's values can differ from those of the
+                // one-node path by FP32 rounding; the stored FP16 values
+                // then differ by at most one rounding step)
                 float2 f2[9], h2[9], fo2[9], ho2[9];
                 const float2 sc = make_float2(k.scale, k.scale);
 #pragma unroll
-                for (int i = 1; i < 9; ++i) f2[i] = __fmul2_rn(__half22float2(pk[i - 1]), sc);
+                for (int i = 1; i < 9; ++i) f2[i] = lmul(__half22float2(pk[i - 1]), sc);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) h2[i] = __fmul2_rn(__half22float2(pk[8 + i]), sc);
+                for (int i = 0; i < 9; ++i) h2[i] = lmul(__half22float2(pk[8 + i]), sc);
                 const LaneState<float2> st = lane_moments<float2>(k, f2, h2, y);
                 lane_collide<float2>(k, st, fo2, ho2, k.inv_scale);
                 const Dither dither((uint32_t)at, step);
@@ -349,20 +354,13 @@ __device__ __forceinline__ void staged_rows_pair(const KConst<float>& k, const _
             if (!(n == 0 ? act0 : act1)) continue;
             float f[9], h[9];
 #pragma unroll
-            for (int i = 1; i < 9; ++i)
-                f[i] = __fmul_rn(n == 0 ? __low2float(pk[i - 1]) : __high2float(pk[i - 1]), k.scale);
+            for (int i = 1; i < 9; ++i) f[i] = (n == 0 ? __low2float(pk[i - 1]) : __high2float(pk[i - 1])) * k.scale;
 #pragma unroll
-            for (int i = 0; i < 9; ++i)
-                h[i] = __fmul_rn(n == 0 ? __low2float(pk[8 + i]) : __high2float(pk[8 + i]), k.scale);
+            for (int i = 0; i < 9; ++i) h[i] = (n == 0 ? __low2float(pk[8 + i]) : __high2float(pk[8 + i])) * k.scale;
             auto collide = [&](const KConst<float>& kk) {
-                if constexpr (TAU1) {
-                    // the lane form, as the global-load kernel runs it
-                    const LaneState<float> st = lane_moments<float>(kk, f, h, y);
-                    lane_collide<float>(kk, st, fo[n], ho[n], kk.inv_scale);
-                } else {
-                    const FastState<float> st = fast_moments(kk, f, h, y);
-                    fast_collide<float, false>(kk, st, f, h, fo[n], ho[n]);
-                }
+                const FastState<float> st = fast_moments(kk, f, h, y);
+                if constexpr (TAU1) fast_collide<float, true>(kk, st, f, h, fo[n], ho[n], kk.inv_scale);
+                else fast_collide<float, false>(kk, st, f, h, fo[n], ho[n]);
             };
             if constexpr (EPS_FIELD) {
                 KConst<float> kc = k;

@@ -2,11 +2,18 @@
 all four sides).
 
 The staged kernel and the global-load kernel run the same per-node code: at
-tau = 1 they must agree bit for bit, for FP32 and FP16 storage, on lattices
-that span several 128-column bands and 4-row segments with ragged edges, and
-on the smallest lattices the staged kernel takes; the FP32 staged lattice
-also matches the batched kernel.  Away from tau = 1 (with sources) and with
-a porosity field the staged kernel is checked against the FP64 oracle."""
+tau = 1 they must agree bit for bit in FP32, on lattices that span several
+128-column bands and 4-row segments with ragged edges, and on the smallest
+lattices the staged kernel takes; the FP32 staged lattice also matches the
+batched kernel.  In FP16 storage at tau = 1 the staged kernel updates pairs
+of interior nodes with packed FP32 instructions, which may fuse a multiply
+into the add that follows it: after one step every stored value agrees with
+the global-load kernel's to within one FP16 rounding step plus the FP32
+rounding of its cancelling terms (and almost all exactly), and after 60
+steps the moments agree to FP16 noise.  With a
+porosity field both kernels run the one-node code and agree bit for bit.
+Away from tau = 1 (with sources) and with a porosity field the staged kernel
+is checked against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -39,12 +46,23 @@ def test_staged_step_matches_global_loads(precision, nx, ny):
     smallest lattices the staged kernel takes (4 rows, one partial band)."""
     p = W.cavity(nx, 1e5, 1e-3, 0.5, ny=ny)
     fields = W.random_fields(p, seed=nx + ny, amp_u=2e-3, amp_T=0.3)
+    if precision == "f16":
+        _fp16_pairs_within_one_rounding_step(p, fields)
     a = _run(p, precision, fields, 60, True)
     b = _run(p, precision, fields, 60, False)
     fa, ga = a.get_state()
     fb, gb = b.get_state()
-    assert np.array_equal(fa[1:], fb[1:]) and np.array_equal(ga, gb)
     ma = a.moments()
+    if precision == "f32":
+        assert np.array_equal(fa[1:], fb[1:]) and np.array_equal(ga, gb)
+    else:
+        mb = b.moments()
+        # FP16 storage noise: the rare different roundings of the first step
+        # spread over 60 steps (the FP16 forms are held to 3e-3 against the
+        # oracle over 2000 steps)
+        assert np.abs(ma["T"] - mb["T"]).max() <= 1e-3
+        du = np.sqrt((ma["ux"] - mb["ux"]) ** 2 + (ma["uy"] - mb["uy"]) ** 2)
+        assert np.linalg.norm(du) <= 1e-2 * np.linalg.norm(np.sqrt(mb["ux"] ** 2 + mb["uy"] ** 2))
     assert np.all(np.isfinite(ma["T"]))
     if precision == "f32":
         bt = lbm.Batch([p], "f32")
@@ -55,6 +73,44 @@ def test_staged_step_matches_global_loads(precision, nx, ny):
         for k in ("ux", "uy", "T", "p"):
             assert np.array_equal(ma[k], mb[k]), k
         bt.close()
+
+
+W_I = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+FP16_SCALE = 2.0 ** -10  # stored value = population / scale (lbm_host.h)
+
+
+def _fp16_step(v):
+    """The FP16 rounding step at the magnitude of v in population units:
+    2^(floor(log2 |v|) - 10), and the subnormal step 2^-24 below 2^-14
+    (both times the storage scale)."""
+    a = np.maximum(np.abs(v), 1e-30)
+    return np.maximum(np.exp2(np.floor(np.log2(a)) - 10), 2.0 ** -24 * FP16_SCALE)
+
+
+def _fp16_pairs_within_one_rounding_step(p, fields):
+    """One step from the same fields: the stored FP16 values of the staged
+    kernel (node pairs, packed arithmetic) and of the global-load kernel
+    (one node, scalar arithmetic) differ by at most one rounding step, and
+    only where the FP32 values fall on different sides of a random rounding
+    threshold (rare)."""
+    a = _run(p, "f16", fields, 1, True)
+    b = _run(p, "f16", fields, 1, False)
+    fa, ga = a.get_state()
+    fb, gb = b.get_state()
+    # thermal values are stored as deviations from w_i sigma T0
+    base = (W_I * p["sigma"] * 0.5 * (p["Th"] + p["Tc"]))[:, None, None]
+    sa = np.concatenate([fa[1:], ga - base])
+    sb = np.concatenate([fb[1:], gb - base])
+    diff = np.abs(sa - sb)
+    # one rounding step at the value, plus the FP32 rounding of the terms
+    # that cancel in it (a few units in the last place of the plane's
+    # largest magnitude)
+    plane_max = np.abs(sb).max(axis=(1, 2), keepdims=True)
+    bound = _fp16_step(np.maximum(np.abs(sa), np.abs(sb))) + 2.0 ** -20 * plane_max
+    assert (diff <= bound).all(), (diff / bound).max()
+    assert (diff > 0).mean() <= 1e-2, (diff > 0).mean()
 
 
 @pytest.mark.parametrize("precision", ["f32", "f16"])
