@@ -54,12 +54,12 @@ constexpr long long kTWaitPolls = 1ll << 28;             // ... or after this ma
 // the band so that its x coordinate stays a multiple of 16 bytes; a copy's
 // shared-memory destination must be 128-byte aligned, so each plane row of a
 // slot is padded to a multiple of 128 bytes.
-template <class S, int BAND, int ROWS>
+template <class S, int BAND, int ROWS, int HALO = 16 / (int)sizeof(S)>
 struct StageLayout {
     using type = S;
     static constexpr int band = BAND;
     static constexpr int rows = ROWS;
-    static constexpr int halo = 16 / (int)sizeof(S);                        // 4 (FP32), 8 (FP16)
+    static constexpr int halo = HALO;                                       // 4 (FP32), LBM_H_INNER (FP16)
     static constexpr int box = BAND + 2 * halo;                             // columns copied per plane row
     static constexpr int plane = ((box * (int)sizeof(S) + 127) / 128) * 128 / (int)sizeof(S);
     static constexpr int slot = NPLANES * plane;                            // elements per slot
@@ -80,7 +80,13 @@ template <> struct TmaLayoutOf<float> { using type = StageLayout<float, kTBand, 
 #define LBM_TMA_ROWS_H 4
 #endif
 constexpr int kHRows = LBM_TMA_ROWS_H;
-template <> struct TmaLayoutOf<__half> { using type = StageLayout<__half, 2 * kTBand, kHRows>; };
+// FP16 copies are 4-D boxes whose innermost dimension holds LBM_H_INNER
+// columns; the band's halo is one such group on each side.
+#ifndef LBM_H_INNER
+#define LBM_H_INNER 32
+#endif
+constexpr int kHInner = LBM_H_INNER;
+template <> struct TmaLayoutOf<__half> { using type = StageLayout<__half, 2 * kTBand, kHRows, kHInner>; };
 template <class S> using TmaLayout = typename TmaLayoutOf<S>::type;
 // Resident blocks per SM the kernels are compiled for (registers: 65536 /
 // (threads x blocks) each): FP16 threads carry two nodes.
@@ -127,7 +133,7 @@ __device__ __forceinline__ void tma_load_slot(const CUtensorMap* tm, S* slot, ui
             asm volatile(
                 "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
                 "%4, %5}], [%6];" ::"r"(smem_addr(slot + p * L::plane)),
-                "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(x >> 3), "r"(y + plane_dy(p)), "r"(p), "r"(b)
+                "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(x / kHInner), "r"(y + plane_dy(p)), "r"(p), "r"(b)
                 : "memory");
         else
             asm volatile(
@@ -631,10 +637,13 @@ bool make_step_tensor_map(const KConst<float>& k, const S* buf, CUtensorMap* out
     if constexpr (sizeof(S) == 2) {
         // (8 columns, column groups, rows, planes); the pitch is a multiple of
         // 64 columns, so every group of 8 up to nx rounded up lies in the row
-        static_assert(TmaLayout<S>::box % 8 == 0, "FP16 boxes are whole groups of 8 columns");
-        const cuuint64_t dims[4] = {8u, (cuuint64_t)((k.nx + 7) / 8), (cuuint64_t)k.ny, (cuuint64_t)NPLANES};
-        const cuuint64_t strides[3] = {8 * sizeof(S), (cuuint64_t)k.pitch * sizeof(S), (cuuint64_t)k.plane * sizeof(S)};
-        const cuuint32_t box[4] = {8u, (cuuint32_t)(TmaLayout<S>::box / 8), 1u, 1u};
+        constexpr int g = kHInner;
+        static_assert(TmaLayout<S>::box % g == 0, "FP16 boxes are whole groups of columns");
+        static_assert(g * sizeof(S) % 16 == 0 && 64 % g == 0, "groups of 16-byte multiples dividing the pitch");
+        const cuuint64_t dims[4] = {(cuuint64_t)g, (cuuint64_t)((k.nx + g - 1) / g), (cuuint64_t)k.ny,
+                                    (cuuint64_t)NPLANES};
+        const cuuint64_t strides[3] = {g * sizeof(S), (cuuint64_t)k.pitch * sizeof(S), (cuuint64_t)k.plane * sizeof(S)};
+        const cuuint32_t box[4] = {(cuuint32_t)g, (cuuint32_t)(TmaLayout<S>::box / g), 1u, 1u};
         return encode(out, TmaType<S>::value, 4, const_cast<S*>(buf), dims, strides, box, estr,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
