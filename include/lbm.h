@@ -25,7 +25,9 @@
  *   Wall nodes are the outermost nodes; the characteristic length defaults to
  *   L = nx - 1.
  * on_device: 0 = the pointers are host memory (the call copies through a
- *   device staging area and returns after the copy); 1 = the pointers are
+ *   device staging area and returns after the copy; input fields in
+ *   page-locked host memory are instead read in place by the kernel that
+ *   consumes them, and the call returns once it has); 1 = the pointers are
  *   device memory of the handle's device (the call is asynchronous on the
  *   handle's stream).
  * Ownership: the caller owns every pointer it passes; nothing is retained
@@ -60,9 +62,13 @@ typedef enum {
     LBM_ERR_GUARD = -7         /* a guard word of the workspace was overwritten */
 } lbm_status;
 
-/* Storage type of the populations.  LBM_F64 computes in FP64, LBM_F32 in
- * FP32; both store the flow populations f_1..f_8 as they are and the thermal
- * populations as deviations g_i - w_i sigma T0 from the rest state. */
+/* Storage type of the populations.  LBM_F64 computes in FP64, LBM_F32 and
+ * LBM_F16 in FP32; all store the flow populations f_1..f_8 as they are and
+ * the thermal populations as deviations g_i - w_i sigma T0 from the rest
+ * state.  LBM_F16 stores them scaled by 2^10 and rounded stochastically
+ * (rounded up with probability equal to the discarded fraction, random bits
+ * from a counter-based hash of the node pair and the step), so that every
+ * stored value is exact in expectation. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2 } lbm_precision;
 
 /* Boundary kind of one side. */
@@ -134,8 +140,12 @@ lbm_status lbm_set_moment_segments(lbm_handle* h, int32_t segments);
  * (LBM_ERR_ARG where it is unavailable: FP64, a periodic side, the moment
  * state, a lattice under 4 x 4, or a CUDA driver without tensor-map encoding).
  * Both kernels run the same per-node arithmetic (results agree to rounding;
- * bit for bit at tau_f = tau_T = 1).  lbm_step_staged returns 1 when the
- * next step uses staged rows, else 0. */
+ * bit for bit in FP32 at tau_f = tau_T = 1).  In FP16 at tau_f = tau_T = 1
+ * the staged kernel computes pairs of interior nodes with packed FP32
+ * instructions, whose fused multiply-adds can round differently: its stored
+ * values then agree with the other kernel's to within one FP16 rounding
+ * step plus FP32 rounding.  lbm_step_staged returns 1 when the next step
+ * uses staged rows, else 0. */
 lbm_status lbm_set_step_staging(lbm_handle* h, int32_t staged);
 int32_t lbm_step_staged(const lbm_handle* h);
 

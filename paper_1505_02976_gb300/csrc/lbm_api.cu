@@ -67,6 +67,27 @@ lbm_status copy_in(lbm_handle* h, double* dst, const double* src, int on_device)
     return LBM_OK;
 }
 
+// Where a kernel reads an input field from: a host field in page-locked
+// memory is read in place through its device mapping (on this machine the
+// GPU reads host memory over the coherent chip-to-chip link, with no staging
+// copy); any other host field is copied into the staging area `stage` first,
+// and device fields are copied there too.  The caller synchronises before
+// returning, so the host array need not outlive the call.
+lbm_status field_source(lbm_handle* h, double* stage, const double* src, int on_device, const double** out) {
+    if (!on_device) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, src) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer) {
+            *out = (const double*)a.devicePointer;
+            return LBM_OK;
+        }
+        (void)cudaGetLastError();  // an unregistered pointer is not an error here
+    }
+    lbm_status s = copy_in(h, stage, src, on_device);
+    if (s != LBM_OK) return s;
+    *out = stage;
+    return LBM_OK;
+}
+
 // Moment state: bring the expansion buffer up to date with the moments (a
 // no-op with population storage, or when nothing changed since the last one).
 lbm_status ensure_pops(lbm_handle* h) {
@@ -255,12 +276,13 @@ lbm_status lbm_set_fields(lbm_handle* h, const double* T, const double* ux, cons
             for (size_t i = 0; i < N; ++i)
                 if (!(eps_field[i] > 0.0 && eps_field[i] < 1.0))
                     return fail(h, LBM_ERR_PARAM_RANGE, "porosity field values must lie in (0, 1)");
-        lbm_status s0 = copy_in(h, F + 3 * N, eps_field, on_device);
+        const double* deps = nullptr;
+        lbm_status s0 = field_source(h, F + 3 * N, eps_field, on_device, &deps);
         if (s0 != LBM_OK) return s0;
         char* area = h->ws + h->L.off_eps;
         cudaError_t e = h->prm.precision == LBM_F64
-                            ? lbm::launch_convert<double>(F + 3 * N, (double*)area, (long long)N, h->stream)
-                            : lbm::launch_convert<float>(F + 3 * N, (float*)area, (long long)N, h->stream);
+                            ? lbm::launch_convert<double>(deps, (double*)area, (long long)N, h->stream)
+                            : lbm::launch_convert<float>(deps, (float*)area, (long long)N, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "porosity field");
         h->k64.eps_field = (const double*)area;
         h->k32.eps_field = (const float*)area;
@@ -272,9 +294,9 @@ lbm_status lbm_set_fields(lbm_handle* h, const double* T, const double* ux, cons
     const double* dux = nullptr;
     const double* duy = nullptr;
     lbm_status s;
-    if (T) { if ((s = copy_in(h, F, T, on_device)) != LBM_OK) return s; dT = F; }
-    if (ux) { if ((s = copy_in(h, F + N, ux, on_device)) != LBM_OK) return s; dux = F + N; }
-    if (uy) { if ((s = copy_in(h, F + 2 * N, uy, on_device)) != LBM_OK) return s; duy = F + 2 * N; }
+    if (T && (s = field_source(h, F, T, on_device, &dT)) != LBM_OK) return s;
+    if (ux && (s = field_source(h, F + N, ux, on_device, &dux)) != LBM_OK) return s;
+    if (uy && (s = field_source(h, F + 2 * N, uy, on_device, &duy)) != LBM_OK) return s;
     h->cur = 0;
     cudaError_t e;
     if (h->moments_kind()) {
