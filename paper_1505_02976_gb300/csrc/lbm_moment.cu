@@ -21,9 +21,11 @@
 // registers only the values still to be pulled (the six moving up, the five
 // moving along x and staying, the six moving down), and takes its x
 // neighbours' values by warp shuffles (12 per node).  No shared memory and
-// no block barrier: a wall node reads its x_f and x_ff neighbours back from
-// the output after a warp barrier, and they always lie in the same strip
-// (strips are at least 3 columns wide, segments at least 3 rows tall).
+// no block barrier: the x_f and x_ff neighbours of a wall node always lie in
+// the same strip (strips are at least 3 columns wide, segments at least 3
+// rows tall); a W or E wall node takes their new moments from their lanes by
+// shuffles, an S or N wall row reads them back from the output after a warp
+// barrier.
 // Every node is expanded once per strip and segment it borders (2 halo
 // columns per 30, 2 halo rows per segment).
 #include <math.h>
@@ -40,7 +42,6 @@ namespace lbm {
 
 constexpr int kMBlock = 128;     // threads per block: four independent warps
 constexpr int kMStrip = 30;      // output columns of a strip, at most (32 lanes with the halo)
-constexpr int kMaxDevices = 64;
 #ifndef LBM_MOMENT_BLOCKS
 #define LBM_MOMENT_BLOCKS 5
 #endif
@@ -88,23 +89,17 @@ __device__ __forceinline__ void store_moments(const KConst<R>& k, R* dst, long l
     d[MGY * pl] = s.gy;
 }
 
-// Boundary state of wall node (x, y) from the new moments of x_f and the new
-// temperature of x_ff (read back from dst, written earlier in this launch by
-// this block), Sec. 3.4 as in wall_state.
+// Boundary state of wall node (x, y) from m, the new moments of its x_f node,
+// and thff, the new temperature of its x_ff node (Sec. 3.4, as wall_state).
 template <class R>
-__device__ __forceinline__ void wall_moments(const KConst<R>& k, R* dst, int x, int y) {
+__device__ __forceinline__ void wall_store(const KConst<R>& k, R* dst, int x, int y, R* m, R thff) {
     const WallInfo w = classify(k, x, y);
-    const long long af = (long long)w.ys * k.pitch + w.xs;
-    R m[kMPlanes];
-#pragma unroll
-    for (int q = 0; q < kMPlanes; ++q) m[q] = dst[q * k.plane + af];
     m[MUX] = k.u_bc[w.uside][0];
     m[MUY] = k.u_bc[w.uside][1];
     if (w.tside >= 0) {
         m[MTH] = k.T_bc[w.tside] - k.T0;
     } else {
         // Eq. (TNEESApGra): T_b = (4 T(x_f) - T(x_ff)) / 3, zero normal gradient
-        const R thff = dst[MTH * k.plane + (long long)w.yff * k.pitch + w.xff];
         m[MTH] = (R(4) * m[MTH] - thff) * (R(1) / R(3));
         if (w.fixgx) m[MGX] = R(0);
         if (w.fixgy) m[MGY] = R(0);
@@ -113,6 +108,19 @@ __device__ __forceinline__ void wall_moments(const KConst<R>& k, R* dst, int x, 
 #pragma unroll
     for (int q = 0; q < kMPlanes; ++q) dst[q * k.plane + at] = m[q];
     if (!isfinite(m[MTH] + m[MP])) atomicOr(k.flag, 1);
+}
+
+// Boundary state of an S or N wall node (x, y), its x_f and x_ff neighbours
+// read back from dst (written earlier in this launch by this warp).
+template <class R>
+__device__ __forceinline__ void wall_moments(const KConst<R>& k, R* dst, int x, int y) {
+    const WallInfo w = classify(k, x, y);
+    const long long af = (long long)w.ys * k.pitch + w.xs;
+    R m[kMPlanes];
+#pragma unroll
+    for (int q = 0; q < kMPlanes; ++q) m[q] = dst[q * k.plane + af];
+    const R thff = dst[MTH * k.plane + (long long)w.yff * k.pitch + w.xff];
+    wall_store(k, dst, x, y, m, thff);
 }
 
 // Values of an expanded node that later rows pull: moving up (f2, f5, f6,
@@ -234,19 +242,37 @@ k_step_m(const __grid_constant__ KConst<R> k, const R* __restrict__ src, R* dst,
         h[8] = __shfl_up_sync(0xffffffffu, ep.dn[5], 1);
         const bool wall_row = (wallS && y == 0) || (wallN && y == k.ny - 1);
         if (!wall_row) {
+            FastState<R> s = {};
             if (out_col && !wall_col) {
                 const long long at = (long long)y * k.pitch + x;
                 if constexpr (EPS_FIELD) {
                     KConst<R> kc = k;
                     apply_eps(kc, node_eps(k, x, y));
-                    store_moments(k, dst, at, fast_moments(kc, f, h, y));
+                    s = fast_moments(kc, f, h, y);
                 } else {
-                    store_moments(k, dst, at, fast_moments(k, f, h, y));
+                    s = fast_moments(k, f, h, y);
                 }
+                store_moments(k, dst, at, s);
             }
             if (wallWE) {
-                __syncwarp();  // x_f, x_ff of the W/E wall nodes are in this row, in this strip
-                if (wall_col) wall_moments(k, dst, x, y);
+                // x_f and x_ff of a W or E wall node are the nodes one and two
+                // columns inward in this row and strip: their new moments come
+                // from those lanes' registers (a read back from dst would hold
+                // the whole warp on a memory round trip every row)
+                const int in = x == 0 ? 1 : -1;
+                const int lf = wall_col ? lane + in : lane, lff = wall_col ? lane + 2 * in : lane;
+                R mf[kMPlanes];
+                mf[MP] = __shfl_sync(0xffffffffu, s.p, lf);
+                mf[MUX] = __shfl_sync(0xffffffffu, s.ux, lf);
+                mf[MUY] = __shfl_sync(0xffffffffu, s.uy, lf);
+                mf[MSXX] = __shfl_sync(0xffffffffu, s.Sxx, lf);
+                mf[MSYY] = __shfl_sync(0xffffffffu, s.Syy, lf);
+                mf[MSXY] = __shfl_sync(0xffffffffu, s.Sxy, lf);
+                mf[MTH] = __shfl_sync(0xffffffffu, s.th, lf);
+                mf[MGX] = __shfl_sync(0xffffffffu, s.gx, lf);
+                mf[MGY] = __shfl_sync(0xffffffffu, s.gy, lf);
+                const R thff = __shfl_sync(0xffffffffu, s.th, lff);
+                if (wall_col) wall_store(k, dst, x, y, mf, thff);
             }
         } else if (y == k.ny - 1) {
             __syncwarp();  // rows ny-2, ny-3 of this strip are complete
@@ -333,8 +359,8 @@ cudaError_t launch_m(const KConst<R>& k, const R* src, R* dst, int nstrips, int 
 template <class R>
 int moment_segments_default(const KConst<R>& k) {
     // two waves of resident warps (segments of >= 3 rows; moment_shape clamps):
-    // at 2048^2, 53.4 GLUPS against 51.2-52.9 for one wave and 44.2 for 1.2
-    // waves (the tail of a partial wave)
+    // at 2048^2 one and two waves measure alike (52-58 GLUPS from box to
+    // box), 1.2 waves 44.2 (the tail of a partial wave)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
