@@ -197,6 +197,18 @@ __device__ __forceinline__ void staged_issue(const CUtensorMap* tm, S* stage, ui
         tma_load_slot(tm, stage + (r - yb) * TmaLayout<S>::slot, bar + (r - yb), x0 - TmaLayout<S>::halo, r);
 }
 
+// The same copies issued by lane 0 of every warp, one row each (warp w takes
+// rows yb + w, yb + w + warps, ...), so that the rows' copies leave together.
+// The barriers must be initialised and visible to every warp.
+template <class S>
+__device__ __forceinline__ void staged_issue_warps(const CUtensorMap* tm, S* stage, uint64_t* bar, int x0, int y0,
+                                                   int rows, int ny) {
+    const int yb = max(y0, 1), ye = min(min(y0 + rows, ny), ny - 1);
+    if ((threadIdx.x & 31) != 0) return;
+    for (int r = yb + (int)(threadIdx.x >> 5); r < ye; r += (int)(blockDim.x >> 5))
+        tma_load_slot(tm, stage + (r - yb) * TmaLayout<S>::slot, bar + (r - yb), x0 - TmaLayout<S>::halo, r);
+}
+
 // One block of the staged step once its copies are issued and its barriers
 // are visible: columns x0 .. x0 + 127 and rows y0 .. y0 + rows - 1 (rows <=
 // kTRows) of the lattice k with population buffers src / dst.  step: the
@@ -422,10 +434,10 @@ k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUte
     if (step & 1u) seg = by == 0 ? nseg - 1 : (by == 1 ? 0 : nseg - by);
 #endif
     const int x0 = blockIdx.x * TmaLayout<S>::band, y0 = seg * rows;
-    __syncthreads();  // barriers initialised (the other threads go on while thread 0 issues)
+    __syncthreads();  // barriers initialised
     // the previous step's writes must be visible before the first copy
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (threadIdx.x == 0) staged_issue<S>(&tm, stage, bar, x0, y0, rows, k.ny);
+    staged_issue_warps<S>(&tm, stage, bar, x0, y0, rows, k.ny);
     if constexpr (std::is_same<S, __half>::value)
         staged_rows_pair<EPS_FIELD, TAU1>(k, src, dst, x0, y0, rows, step, stage, bar);
     else
@@ -434,10 +446,11 @@ k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUte
 
 // The staged step of a batch of FP32 cavities walled on all four sides: block
 // i takes work item i = (cavity, band origin x0, segment origin y0, cavity
-// height) of the work list.  Thread 0 issues the block's copies
-// (the cavity's tensor map for the source buffer is read from global
-// memory) as soon as the previous step has finished, while the block copies
-// the cavity's constants into shared memory.
+// height) of the work list.  The block copies the cavity's constants into
+// shared memory; once the previous step has finished, lane 0 of each warp
+// issues the copies of one row (the cavity's tensor map for the source
+// buffer is read from global memory) and every thread goes on to the wall
+// nodes and its rows.
 __global__ void __launch_bounds__(kTBand, TmaLayout<float>::blocks)
 k_step_batch_tma(const BatchCavity<float>* __restrict__ cav, const CUtensorMap* __restrict__ maps,
                  const StagedItem* __restrict__ items, const float* __restrict__ src, float* __restrict__ dst,
@@ -456,10 +469,10 @@ k_step_batch_tma(const BatchCavity<float>* __restrict__ cav, const CUtensorMap* 
     int* to = reinterpret_cast<int*>(&ks);
     for (int q = threadIdx.x; q < (int)(sizeof(KConst<float>) / sizeof(int)); q += kTBand) to[q] = from[q];
     if (threadIdx.x == 0) off = cav[w.cavity].offset;
+    __syncthreads();  // constants, offset and barriers
     // the previous step's writes must be visible before the copies
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    if (threadIdx.x == 0) staged_issue<float>(maps + w.cavity, stage, bar, w.x0, w.y0, kTRows, w.ny);
-    __syncthreads();  // constants, offset and barriers
+    staged_issue_warps<float>(maps + w.cavity, stage, bar, w.x0, w.y0, kTRows, w.ny);
     if (ks.omf == 0.f && ks.omT == 0.f)
         staged_rows<float, false, true>(ks, src + off, dst + off, w.x0, w.y0, kTRows, step, stage, bar);
     else
