@@ -245,6 +245,18 @@ def cpu_baseline_leg() -> dict:
             "runs": runs}
 
 
+def workload_config(world: int) -> dict:
+    """The benchmark workload as both arms name it in their JSON lines."""
+    n = WORKLOAD["n"]
+    planes, what = (9, "moments") if WORKLOAD["state"] == "moments" else (17, "populations")
+    mb = n * n * planes * 4 / 1e6
+    return {"workload": WORKLOAD["name"], "nx": n, "ny": n, "Ra": WORKLOAD["Ra"], "Da": WORKLOAD["Da"],
+            "eps": WORKLOAD["eps"], "Pr": WORKLOAD["Pr"], "storage": WORKLOAD["precision"],
+            "state": WORKLOAD["state"], "replicas": world,
+            "l2": f"inputs larger than L2: {mb:.0f} MB of {what} read and {mb:.0f} MB written per step "
+                  "(L2 129 MB), no flush needed"}
+
+
 def run_reference(args):
     """The reference arm: the FP64 oracle on the benchmark workload itself
     (the same 2048 x 2048 cavity and groups), every host processor, one full
@@ -263,16 +275,14 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = n * n * args.steps / dt / 1e6
     cores = oracle.threads()
-    sample = (f"{n}x{n} cavity (the benchmark workload), {args.steps} oracle time steps after "
+    sample = (f"{n}x{n} cavity (the benchmark workload), {args.steps} time steps of the FP64 oracle after "
               f"{args.warmup} of warm-up, {cores} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"], "nx": n, "ny": n,
-                   "Ra": WORKLOAD["Ra"], "Da": WORKLOAD["Da"], "eps": WORKLOAD["eps"],
-                   "Pr": WORKLOAD["Pr"], "storage": "f64 (oracle)", "state": "populations"},
+        "config": workload_config(world),
         "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                          "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -534,11 +544,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], "nx": n, "ny": n, "Ra": WORKLOAD["Ra"],
-                       "Da": WORKLOAD["Da"], "eps": WORKLOAD["eps"], "Pr": WORKLOAD["Pr"],
-                       "storage": prec, "state": WORKLOAD["state"], "replicas": world,
-                       "l2": "inputs larger than L2: 285 MB of populations read and 285 MB "
-                             "written per step (L2 129 MB), no flush needed"},
+            "config": workload_config(world),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
