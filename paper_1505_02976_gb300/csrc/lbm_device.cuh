@@ -101,6 +101,9 @@ struct KConst {
     R fA_ep, fA_uu, fA_tr, fA_uF, f_cu2, f_ScS, f_cucF, f_cu, f_cF;
     R h_sig, h_uu, h_pT, h_kQ, h_cu2, h_u3, h_ug, h_uQ, h_g, h_W;
     R h0_sig, h0_uu, h0_pT, h0_kQ;
+    // nodes at the end of a step's sweep whose FP32 stores ask L2 to keep
+    // them (evict-last hint): the next step reads those rows first (0: none)
+    long long l2_hot;
 };
 
 // Population storage conversion.
@@ -119,12 +122,28 @@ __device__ __forceinline__ void store_pop<__half, float>(__half* p, float v, flo
 
 // Store of the 17 post-collision values of one node; FP16 storage rounds
 // stochastically (dither != nullptr) or to nearest (lbm_half.cuh).
+// evict_last (FP32 storage): the stores carry an L2 evict-last policy.
 template <class S, class R>
 __device__ __forceinline__ void store_planes(S* __restrict__ d, long long pl, const R* fo, const R* ho,
-                                             float inv_scale, Dither* dither) {
+                                             float inv_scale, Dither* dither, bool evict_last = false) {
     if constexpr (std::is_same<S, __half>::value) {
         store_planes_half<R>(d, pl, fo, ho, inv_scale, dither);
     } else {
+        if constexpr (std::is_same<S, float>::value) {
+            if (evict_last) {
+                uint64_t pol;
+                asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+#pragma unroll
+                for (int i = 1; i < 9; ++i)
+                    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(d + (i - 1) * pl),
+                                 "f"(float(fo[i])), "l"(pol) : "memory");
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(d + (8 + i) * pl),
+                                 "f"(float(ho[i])), "l"(pol) : "memory");
+                return;
+            }
+        }
 #pragma unroll
         for (int i = 1; i < 9; ++i) d[(i - 1) * pl] = S(fo[i]);
 #pragma unroll

@@ -213,10 +213,11 @@ __device__ __forceinline__ void staged_issue_warps(const CUtensorMap* tm, S* sta
 // are visible: columns x0 .. x0 + 127 and rows y0 .. y0 + rows - 1 (rows <=
 // kTRows) of the lattice k with population buffers src / dst.  step: the
 // step number (the stochastic rounding of FP16 stores draws from it).
+// hot: the block's stores ask L2 to keep them (FP32).
 template <class S, bool EPS_FIELD, bool TAU1>
 __device__ __forceinline__ bool staged_rows(const KConst<float>& k, const S* __restrict__ src, S* __restrict__ dst,
                                             int x0, int y0, int rows, uint32_t step, const S* stage, uint64_t* bar,
-                                            uint32_t phases = 0u) {
+                                            uint32_t phases = 0u, bool hot = false) {
     using L = TmaLayout<S>;
     const int tid = threadIdx.x;
     const int y1 = min(y0 + rows, k.ny);
@@ -268,7 +269,7 @@ __device__ __forceinline__ bool staged_rows(const KConst<float>& k, const S* __r
             }
             const int at = y * k.pitch + x;
             Dither dither((uint32_t)at, step);
-            store_planes<S, float>(dst + at, k.plane32, fo, ho, prescale ? 1.0f : k.inv_scale, &dither);
+            store_planes<S, float>(dst + at, k.plane32, fo, ho, prescale ? 1.0f : k.inv_scale, &dither, hot);
         }
     }
     if (!ok) {
@@ -434,6 +435,9 @@ k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUte
     if (step & 1u) seg = by == 0 ? nseg - 1 : (by == 1 ? 0 : nseg - by);
 #endif
     const int x0 = blockIdx.x * TmaLayout<S>::band, y0 = seg * rows;
+    // the segments the hardware starts last (the last k.l2_hot nodes of the
+    // sweep) are the rows the next step, sweeping the other way, reads first
+    const bool hot = (long long)(nseg - by) * rows * k.nx <= k.l2_hot;
     __syncthreads();  // barriers initialised
     // the previous step's writes must be visible before the first copy
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -441,7 +445,7 @@ k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUte
     if constexpr (std::is_same<S, __half>::value)
         staged_rows_pair<EPS_FIELD, TAU1>(k, src, dst, x0, y0, rows, step, stage, bar);
     else
-        staged_rows<S, EPS_FIELD, TAU1>(k, src, dst, x0, y0, rows, step, stage, bar);
+        staged_rows<S, EPS_FIELD, TAU1>(k, src, dst, x0, y0, rows, step, stage, bar, 0u, hot);
 }
 
 // The staged step of a batch of FP32 cavities walled on all four sides: block
