@@ -72,3 +72,8 @@ def test_reference_arm_under_two_ranks():
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["unit"] == "MLUPS"
     assert line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+    # the same workload config the GPU arm prints (one helper builds both)
+    sys.path.insert(0, ROOT)
+    import bench
+    assert line["config"] == bench.workload_config(2)
+    assert line["metric"] == bench.METRIC and line["higher_is_better"] is True
