@@ -108,22 +108,23 @@ lbm_status ensure_pops(lbm_handle* h) {
         if (s_ != LBM_OK) return s_;                 \
     } while (0)
 
-// Nodes at the end of an FP32 step's sweep whose stores ask L2 to keep them
+// Nodes at the end of a staged step's sweep whose stores ask L2 to keep them
 // (evict-last hint; the next step, sweeping the other way, reads those rows
 // first).  Where a step writes at most four L2s, every store: the kept rows
-// outweigh the halo re-reads the copies then lose from L2 (2048^2, 2.2 L2s:
-// 48.75 vs 48.20 GLUPS, the last half L2 only 48.55).  Larger lattices keep
-// only the last half L2 of the sweep (8192^2: every store 49.03 vs 49.46,
-// half an L2 49.40).  0 for the other storages or if the L2 size is unknown;
-// the hint changes no value.
+// outweigh the halo re-reads the copies then lose from L2 (FP32 2048^2,
+// 2.2 L2s: 48.75 vs 48.20 GLUPS, the last half L2 only 48.55).  Larger
+// lattices keep only the last half L2 of the sweep (FP32 8192^2: every
+// store 49.03 vs 49.46, half an L2 49.40; FP16 8192^2: 90.04 vs 89.89).
+// 0 for FP64 (no staged kernel) or if the L2 size is unknown; the hint
+// changes no value.
 long long l2_hot_nodes(const lbm_params* p) {
-    if (p->precision != LBM_F32) return 0;
+    if (p->precision == LBM_F64) return 0;
     int dev = 0, l2 = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
         (void)cudaGetLastError();
         return 0;
     }
-    const long long per_node = lbm::NPLANES * (long long)sizeof(float);
+    const long long per_node = lbm::NPLANES * (p->precision == LBM_F16 ? 2LL : 4LL);
     const long long nodes = (long long)p->nx * p->ny;
     if (nodes * per_node <= 4LL * l2) return nodes;
     return (long long)l2 / 2 / per_node;

@@ -101,7 +101,7 @@ struct KConst {
     R fA_ep, fA_uu, fA_tr, fA_uF, f_cu2, f_ScS, f_cucF, f_cu, f_cF;
     R h_sig, h_uu, h_pT, h_kQ, h_cu2, h_u3, h_ug, h_uQ, h_g, h_W;
     R h0_sig, h0_uu, h0_pT, h0_kQ;
-    // nodes at the end of a step's sweep whose FP32 stores ask L2 to keep
+    // nodes at the end of a staged step's sweep whose stores ask L2 to keep
     // them (evict-last hint): the next step reads those rows first (0: none)
     long long l2_hot;
 };

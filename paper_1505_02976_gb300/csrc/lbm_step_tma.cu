@@ -213,7 +213,8 @@ __device__ __forceinline__ void staged_issue_warps(const CUtensorMap* tm, S* sta
 // are visible: columns x0 .. x0 + 127 and rows y0 .. y0 + rows - 1 (rows <=
 // kTRows) of the lattice k with population buffers src / dst.  step: the
 // step number (the stochastic rounding of FP16 stores draws from it).
-// hot: the block's stores ask L2 to keep them (FP32).
+// hot: the block's stores ask L2 to keep them (FP32; the FP16 form below
+// does the same for its interior pairs).
 template <class S, bool EPS_FIELD, bool TAU1>
 __device__ __forceinline__ bool staged_rows(const KConst<float>& k, const S* __restrict__ src, S* __restrict__ dst,
                                             int x0, int y0, int rows, uint32_t step, const S* stage, uint64_t* bar,
@@ -293,7 +294,7 @@ __device__ __forceinline__ bool staged_rows(const KConst<float>& k, const S* __r
 template <bool EPS_FIELD, bool TAU1>
 __device__ __forceinline__ void staged_rows_pair(const KConst<float>& k, const __half* __restrict__ src,
                                                  __half* __restrict__ dst, int x0, int y0, int rows, uint32_t step,
-                                                 const __half* stage, uint64_t* bar) {
+                                                 const __half* stage, uint64_t* bar, bool hot = false) {
     using L = TmaLayout<__half>;
     const int tid = threadIdx.x;
     const int y1 = min(y0 + rows, k.ny);
@@ -360,6 +361,19 @@ __device__ __forceinline__ void staged_rows_pair(const KConst<float>& k, const _
                 const Dither dither((uint32_t)at, step);
                 uint32_t* wd = reinterpret_cast<uint32_t*>(dst + at);
                 const int pw = k.plane32 >> 1;
+                if (hot) {
+                    uint64_t pol;
+                    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+#pragma unroll
+                    for (int i = 1; i < 9; ++i)
+                        asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(wd + (i - 1) * pw),
+                                     "r"(half2_sr(fo2[i].y, fo2[i].x, dither.word(i - 1))), "l"(pol) : "memory");
+#pragma unroll
+                    for (int i = 0; i < 9; ++i)
+                        asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(wd + (8 + i) * pw),
+                                     "r"(half2_sr(ho2[i].y, ho2[i].x, dither.word(8 + i))), "l"(pol) : "memory");
+                    continue;
+                }
 #pragma unroll
                 for (int i = 1; i < 9; ++i) wd[(i - 1) * pw] = half2_sr(fo2[i].y, fo2[i].x, dither.word(i - 1));
 #pragma unroll
@@ -443,7 +457,7 @@ k_step_tma(const __grid_constant__ KConst<float> k, const __grid_constant__ CUte
     asm volatile("griddepcontrol.wait;" ::: "memory");
     staged_issue_warps<S>(&tm, stage, bar, x0, y0, rows, k.ny);
     if constexpr (std::is_same<S, __half>::value)
-        staged_rows_pair<EPS_FIELD, TAU1>(k, src, dst, x0, y0, rows, step, stage, bar);
+        staged_rows_pair<EPS_FIELD, TAU1>(k, src, dst, x0, y0, rows, step, stage, bar, hot);
     else
         staged_rows<S, EPS_FIELD, TAU1>(k, src, dst, x0, y0, rows, step, stage, bar, 0u, hot);
 }
